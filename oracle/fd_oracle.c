@@ -1,0 +1,498 @@
+/*
+ * fd_oracle.c -- FP64 CPU oracle for the time-stepped 3-D finite-difference
+ * wave-propagation sweep of arXiv:1807.03032 (Devito).
+ *
+ * TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only the test-suite, the smoke check
+ * and the benchmark's CPU-baseline leg may load this library.  It shares no
+ * code, header or constant generator with the CUDA path.
+ *
+ * It is written to be read against the paper, not to be fast: plain loops,
+ * FP64 arithmetic, one grid point at a time, no blocking and no fusion.  The
+ * only parallelism is an OpenMP loop over independent grid points, which does
+ * not change any result.  Inputs arrive as FP32 (the exact bits the GPU
+ * receives) and are widened to FP64 on entry.
+ *
+ * Paper passages followed (section / equation / listing labels of the paper):
+ *   - Eq. (WE), section "Symbolic types": m u_tt - lap(u) = q_s, zero initial
+ *     conditions; m = 1/c^2.
+ *   - Listing fd-1 / fd-2 / fd-3, section "Discretization": central FD
+ *     derivatives and the explicit leapfrog update obtained with `solve`.
+ *   - Eq. (interp) and Listing finject: linear (trilinear in 3-D)
+ *     interpolation and injection as its adjoint, scaled dt^2 q / m, added to
+ *     the field at t+1.
+ *   - Section "Test case setup": zero initial conditions, Dirichlet boundary,
+ *     absorbing border, space orders 4..16, second order in time; TTI is two
+ *     coupled acoustic equations whose Laplacians are built from rotated
+ *     first-derivative operators.
+ *   - Section "Domain, halo, and padding regions": the computational domain
+ *     includes the absorbing layers; halo points are ghosts (zero here).
+ *
+ * Readings where the paper is silent (the same readings bind the CUDA path):
+ *   - space order so -> stencil radius r = so/2 for both the compact second
+ *     derivative and the central first derivative;
+ *   - Dirichlet: every grid point is updated, values outside the grid are 0;
+ *   - damping enters as damp * u_t, discretised centrally:
+ *       m (u+ - 2u + u-)/dt^2 + damp (u+ - u-)/(2 dt) = lap(u);
+ *     damp(i,j,k) = dx[i] + dy[j] + dz[k] (sum of per-axis 1-D profiles);
+ *   - injection at step n adds w_c dt^2 q[n] / (m + damp dt/2) to u^{n+1}
+ *     (reduces to the paper's dt^2 q / m where damp = 0);
+ *   - receivers sample u^n for n = 0..nt-1;
+ *   - interpolation index x1 = floor((x-o)/h) clamped to n-2, computed in FP64;
+ *   - TTI (pseudo-acoustic, rotated first derivatives):
+ *       Hz q  = sum_i D_i( n_i * sum_j n_j D_j q ),  L q = sum_i D_i D_i q,
+ *       Hxy q = L q - Hz q,  n = (sin t cos f, sin t sin f, cos t),
+ *       m p_tt + damp p_t = (1+2 eps) Hxy p + sqrt(1+2 delta) Hz r,
+ *       m r_tt + damp r_t = sqrt(1+2 delta) Hxy p + Hz r;
+ *     the source is injected into p and r, receivers record p.
+ *
+ * Layout: C order [z][y][x] (x fastest), index (k*ny + j)*nx + i.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int32_t nx, ny, nz;
+    double hx, hy, hz;
+    double ox, oy, oz;
+} ora_grid;
+
+enum { ORA_OK = 0, ORA_ERR_ARG = -1, ORA_ERR_COORD = -4, ORA_ERR_OOM = -5 };
+
+static size_t npts(const ora_grid *g) { return (size_t)g->nx * g->ny * g->nz; }
+
+static size_t lin(const ora_grid *g, int i, int j, int k) {
+    return ((size_t)k * g->ny + j) * g->nx + i;
+}
+
+static int wrap(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+/* Value of a grid function at (i,j,k).  Outside the grid it is the zero ghost
+ * of the Dirichlet boundary, or the periodic image (a test-only mode used by
+ * the plane-wave pins). */
+static double at(const ora_grid *g, int periodic, const double *f, int i, int j, int k) {
+    if (periodic) {
+        i = wrap(i, g->nx);
+        j = wrap(j, g->ny);
+        k = wrap(k, g->nz);
+    } else if (i < 0 || j < 0 || k < 0 || i >= g->nx || j >= g->ny || k >= g->nz) {
+        return 0.0;
+    }
+    return f[lin(g, i, j, k)];
+}
+
+/* Central FD weights for stencil radius r (space order 2r), closed form.
+ * Second derivative:  w[k] = 2(-1)^(k+1) (r!)^2 / (k^2 (r-k)! (r+k)!),
+ *                     w[0] = -2 sum_k w[k].
+ * First derivative:   c[k] = (-1)^(k+1) (r!)^2 / (k (r-k)! (r+k)!), c[0] = 0.
+ * For r = 1 these are Listing fd-1's [1, -2, 1]/h^2 and +-1/(2h). */
+void ora_fd_weights(int r, double *w, double *c) {
+    double ratio = 1.0; /* (r!)^2 / ((r-k)! (r+k)!) */
+    double sum = 0.0;
+    c[0] = 0.0;
+    for (int k = 1; k <= r; ++k) {
+        ratio *= (double)(r - k + 1) / (double)(r + k);
+        double sgn = (k % 2 == 1) ? 1.0 : -1.0;
+        w[k] = 2.0 * sgn * ratio / ((double)k * (double)k);
+        c[k] = sgn * ratio / (double)k;
+        sum += w[k];
+    }
+    w[0] = -2.0 * sum;
+}
+
+static int radius_of(int so) {
+    if (so < 2 || so > 32 || (so % 2) != 0) return -1;
+    return so / 2;
+}
+
+/* Compact Laplacian: sum over axes of the 1-D central second derivative. */
+int ora_laplacian(const ora_grid *g, int so, int periodic, const double *u, double *out) {
+    int r = radius_of(so);
+    if (r < 0) return ORA_ERR_ARG;
+    double w[33], c[33];
+    ora_fd_weights(r, w, c);
+    const double ih2[3] = {1.0 / (g->hx * g->hx), 1.0 / (g->hy * g->hy), 1.0 / (g->hz * g->hz)};
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 0; k < g->nz; ++k)
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i) {
+                double center = u[lin(g, i, j, k)];
+                double dxx = w[0] * center, dyy = w[0] * center, dzz = w[0] * center;
+                for (int s = 1; s <= r; ++s) {
+                    dxx += w[s] * (at(g, periodic, u, i + s, j, k) + at(g, periodic, u, i - s, j, k));
+                    dyy += w[s] * (at(g, periodic, u, i, j + s, k) + at(g, periodic, u, i, j - s, k));
+                    dzz += w[s] * (at(g, periodic, u, i, j, k + s) + at(g, periodic, u, i, j, k - s));
+                }
+                out[lin(g, i, j, k)] = dxx * ih2[0] + dyy * ih2[1] + dzz * ih2[2];
+            }
+    return ORA_OK;
+}
+
+/* Central first derivative along one axis (0 = x, 1 = y, 2 = z). */
+int ora_first_derivative(const ora_grid *g, int so, int periodic, int axis, const double *f,
+                         double *out) {
+    int r = radius_of(so);
+    if (r < 0 || axis < 0 || axis > 2) return ORA_ERR_ARG;
+    double w[33], c[33];
+    ora_fd_weights(r, w, c);
+    const int di = axis == 0, dj = axis == 1, dk = axis == 2;
+    const double h = axis == 0 ? g->hx : (axis == 1 ? g->hy : g->hz);
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 0; k < g->nz; ++k)
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i) {
+                double d = 0.0;
+                for (int s = 1; s <= r; ++s)
+                    d += c[s] * (at(g, periodic, f, i + s * di, j + s * dj, k + s * dk) -
+                                 at(g, periodic, f, i - s * di, j - s * dj, k - s * dk));
+                out[lin(g, i, j, k)] = d / h;
+            }
+    return ORA_OK;
+}
+
+/* damp(i,j,k) from the per-axis 1-D profiles (NULL = no damping). */
+static double damp_at(const ora_grid *g, const double *damp, int i, int j, int k) {
+    if (!damp) return 0.0;
+    return damp[i] + damp[g->nx + j] + damp[g->nx + g->ny + k];
+}
+
+/* Leapfrog update of the damped acoustic equation at every grid point, from
+ * the Laplacian `lap` of u^n already evaluated:
+ *   m (u+ - 2u + u-)/dt^2 + damp (u+ - u-)/(2dt) = lap
+ *   => u+ = (dt^2 lap + m (2u - u-) + eta u-) / (m + eta),  eta = damp dt/2.
+ * With damp = 0 this is Listing fd-3's u+ = 2u - u- + dt^2 lap / m. */
+static void leapfrog(const ora_grid *g, double dt, const double *m, const double *damp,
+                     const double *lap, const double *u, const double *uprev, double *unext) {
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 0; k < g->nz; ++k)
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i) {
+                size_t p = lin(g, i, j, k);
+                double eta = damp_at(g, damp, i, j, k) * dt * 0.5;
+                unext[p] = (dt * dt * lap[p] + m[p] * (2.0 * u[p] - uprev[p]) + eta * uprev[p]) /
+                           (m[p] + eta);
+            }
+}
+
+/* One acoustic time step u^{n+1} from (u^n, u^{n-1}). */
+int ora_acoustic_step(const ora_grid *g, int so, int periodic, double dt, const double *m,
+                      const double *damp, const double *u, const double *uprev, double *unext) {
+    double *lap = (double *)malloc(npts(g) * sizeof(double));
+    if (!lap) return ORA_ERR_OOM;
+    int st = ora_laplacian(g, so, periodic, u, lap);
+    if (st == ORA_OK) leapfrog(g, dt, m, damp, lap, u, uprev, unext);
+    free(lap);
+    return st;
+}
+
+/* Trilinear stencil of one sparse point (Eq. interp, tensor product over the
+ * three axes): the 8 node indices and FP64 weights.  x1 = floor((x-o)/h),
+ * clamped to n-2 so that a point on the last node uses x1 = n-2, frac = 1. */
+static int sparse_point(const ora_grid *g, const float *xyz, size_t idx[8], double wgt[8]) {
+    const int n[3] = {g->nx, g->ny, g->nz};
+    const double h[3] = {g->hx, g->hy, g->hz};
+    const double o[3] = {g->ox, g->oy, g->oz};
+    int i1[3];
+    double fr[3];
+    for (int a = 0; a < 3; ++a) {
+        double s = ((double)xyz[a] - o[a]) / h[a];
+        if (!(s >= 0.0 && s <= (double)(n[a] - 1))) return ORA_ERR_COORD;
+        int x1 = (int)floor(s);
+        if (x1 > n[a] - 2) x1 = n[a] - 2;
+        i1[a] = x1;
+        fr[a] = s - (double)x1;
+    }
+    for (int c = 0; c < 8; ++c) {
+        int a = c & 1, b = (c >> 1) & 1, d = (c >> 2) & 1;
+        idx[c] = lin(g, i1[0] + a, i1[1] + b, i1[2] + d);
+        wgt[c] = (a ? fr[0] : 1.0 - fr[0]) * (b ? fr[1] : 1.0 - fr[1]) * (d ? fr[2] : 1.0 - fr[2]);
+    }
+    return ORA_OK;
+}
+
+/* Receiver interpolation (Eq. interp): out[i] = sum_c w_c u[node_c]. */
+int ora_interpolate(const ora_grid *g, int npt, const float *xyz, const double *u, double *out) {
+    for (int p = 0; p < npt; ++p) {
+        size_t idx[8];
+        double w[8];
+        int st = sparse_point(g, xyz + 3 * (size_t)p, idx, w);
+        if (st) return st;
+        double acc = 0.0;
+        for (int c = 0; c < 8; ++c) acc += w[c] * u[idx[c]];
+        out[p] = acc;
+    }
+    return ORA_OK;
+}
+
+/* Source injection (Listing finject): u[node_c] += w_c * scale[node_c] * q[p],
+ * accumulated.  `scale` is dt^2/(m + damp dt/2) per node (dt^2/m undamped). */
+int ora_inject(const ora_grid *g, int npt, const float *xyz, const double *q, const double *scale,
+               double *u) {
+    for (int p = 0; p < npt; ++p) {
+        size_t idx[8];
+        double w[8];
+        int st = sparse_point(g, xyz + 3 * (size_t)p, idx, w);
+        if (st) return st;
+        for (int c = 0; c < 8; ++c) u[idx[c]] += w[c] * scale[idx[c]] * q[p];
+    }
+    return ORA_OK;
+}
+
+static double *widen(const float *src, size_t n) {
+    double *d = (double *)malloc(n * sizeof(double));
+    if (d)
+        for (size_t i = 0; i < n; ++i) d[i] = (double)src[i];
+    return d;
+}
+
+static int check_sparse(const ora_grid *g, int npt, const float *xyz) {
+    for (int p = 0; p < npt; ++p) {
+        size_t idx[8];
+        double w[8];
+        if (sparse_point(g, xyz + 3 * (size_t)p, idx, w)) return ORA_ERR_COORD;
+    }
+    return ORA_OK;
+}
+
+/* Injection scale per node: dt^2 / (m + damp dt/2). */
+static void injection_scale(const ora_grid *g, double dt, const double *m, const double *damp,
+                            double *scale) {
+    for (int k = 0; k < g->nz; ++k)
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i) {
+                size_t p = lin(g, i, j, k);
+                scale[p] = dt * dt / (m[p] + damp_at(g, damp, i, j, k) * dt * 0.5);
+            }
+}
+
+/*
+ * Acoustic forward model.  For every shot (shots share m and damp):
+ *   u^0, u^{-1} = u_init (or 0, Eq. WE's zero initial conditions);
+ *   for n = 0 .. nt-2:  u^{n+1} = step(u^n, u^{n-1});
+ *                       inject src[n] into u^{n+1};
+ *                       rec[n] = interp(u^n);
+ *   rec[nt-1] = interp(u^{nt-1});  u_final = (u^{nt-1}, u^{nt-2}).
+ * The per-step order is the paper's schedule of a time iteration: stencil
+ * update, then the sparse injection into the t+1 field.
+ * Array shapes: m [nz][ny][nx]; damp [nx+ny+nz] or NULL; src_xyz
+ * [nshots][nsrc][3]; src_wav [nshots][nt][nsrc]; rec_xyz [nshots][nrec][3];
+ * rec_out [nshots][nt][nrec]; u_init/u_final [nshots][2][nz][ny][nx] or NULL.
+ */
+int ora_acoustic_forward(const ora_grid *g, int so, int periodic, double dt, int nt, int nshots,
+                         const float *m32, const float *damp32, int nsrc, const float *src_xyz,
+                         const float *src_wav, int nrec, const float *rec_xyz, double *rec_out,
+                         const float *u_init, double *u_final) {
+    if (radius_of(so) < 0 || nt < 1 || nshots < 1 || nsrc < 0 || nrec < 0) return ORA_ERR_ARG;
+    const size_t N = npts(g);
+    for (int s = 0; s < nshots; ++s) {
+        if (check_sparse(g, nsrc, src_xyz + (size_t)s * nsrc * 3)) return ORA_ERR_COORD;
+        if (check_sparse(g, nrec, rec_xyz + (size_t)s * nrec * 3)) return ORA_ERR_COORD;
+    }
+    double *m = widen(m32, N);
+    double *damp = damp32 ? widen(damp32, (size_t)g->nx + g->ny + g->nz) : NULL;
+    double *scale = (double *)malloc(N * sizeof(double));
+    double *u = (double *)malloc(N * sizeof(double));
+    double *um = (double *)malloc(N * sizeof(double));
+    double *un = (double *)malloc(N * sizeof(double));
+    double *q = (double *)malloc(((size_t)nsrc + 1) * sizeof(double));
+    int st = ORA_OK;
+    if (!m || (damp32 && !damp) || !scale || !u || !um || !un || !q) {
+        st = ORA_ERR_OOM;
+        goto done;
+    }
+    injection_scale(g, dt, m, damp, scale);
+    for (int s = 0; s < nshots; ++s) {
+        const float *sxyz = src_xyz + (size_t)s * nsrc * 3;
+        const float *rxyz = rec_xyz + (size_t)s * nrec * 3;
+        double *rec = rec_out ? rec_out + (size_t)s * nt * nrec : NULL;
+        for (size_t p = 0; p < N; ++p) {
+            u[p] = u_init ? (double)u_init[((size_t)s * 2 + 0) * N + p] : 0.0;
+            um[p] = u_init ? (double)u_init[((size_t)s * 2 + 1) * N + p] : 0.0;
+        }
+        for (int n = 0; n + 1 < nt; ++n) {
+            st = ora_acoustic_step(g, so, periodic, dt, m, damp, u, um, un);
+            if (st) goto done;
+            for (int p = 0; p < nsrc; ++p) q[p] = (double)src_wav[((size_t)s * nt + n) * nsrc + p];
+            ora_inject(g, nsrc, sxyz, q, scale, un);
+            if (rec) ora_interpolate(g, nrec, rxyz, u, rec + (size_t)n * nrec);
+            double *t = um;
+            um = u;
+            u = un;
+            un = t;
+        }
+        if (rec) ora_interpolate(g, nrec, rxyz, u, rec + (size_t)(nt - 1) * nrec);
+        if (u_final) {
+            memcpy(u_final + ((size_t)s * 2 + 0) * N, u, N * sizeof(double));
+            memcpy(u_final + ((size_t)s * 2 + 1) * N, um, N * sizeof(double));
+        }
+    }
+done:
+    free(m);
+    free(damp);
+    free(scale);
+    free(u);
+    free(um);
+    free(un);
+    free(q);
+    return st;
+}
+
+/*
+ * TTI operators for one field q: Hz q = sum_i D_i(n_i (n . grad q)) and
+ * L q = sum_i D_i D_i q, with n = (sin t cos f, sin t sin f, cos t) per point.
+ * D is the central first derivative of order so; temporaries outside the
+ * grid are zero ghosts (or periodic images).  Evaluated literally: gradient,
+ * projection on n, scaling by n_i, second first-derivative pass.
+ */
+int ora_tti_operators(const ora_grid *g, int so, int periodic, const double *theta,
+                      const double *phi, const double *q, double *hz, double *lq) {
+    const size_t N = npts(g);
+    double *grad[3], *proj, *tmp, *dtmp;
+    int st = ORA_OK;
+    for (int a = 0; a < 3; ++a) grad[a] = (double *)malloc(N * sizeof(double));
+    proj = (double *)malloc(N * sizeof(double));
+    tmp = (double *)malloc(N * sizeof(double));
+    dtmp = (double *)malloc(N * sizeof(double));
+    if (!grad[0] || !grad[1] || !grad[2] || !proj || !tmp || !dtmp) {
+        st = ORA_ERR_OOM;
+        goto done;
+    }
+    /* gradient of q */
+    for (int a = 0; a < 3; ++a) {
+        st = ora_first_derivative(g, so, periodic, a, q, grad[a]);
+        if (st) goto done;
+    }
+    /* projection on the symmetry axis: proj = n . grad q */
+    for (size_t p = 0; p < N; ++p) {
+        double nx = sin(theta[p]) * cos(phi[p]), ny = sin(theta[p]) * sin(phi[p]),
+               nz = cos(theta[p]);
+        proj[p] = nx * grad[0][p] + ny * grad[1][p] + nz * grad[2][p];
+    }
+    if (hz) memset(hz, 0, N * sizeof(double));
+    if (lq) memset(lq, 0, N * sizeof(double));
+    for (int a = 0; a < 3; ++a) {
+        if (hz) {
+            /* hz += D_a (n_a * proj) */
+            for (size_t p = 0; p < N; ++p) {
+                double na = a == 0   ? sin(theta[p]) * cos(phi[p])
+                            : a == 1 ? sin(theta[p]) * sin(phi[p])
+                                     : cos(theta[p]);
+                tmp[p] = na * proj[p];
+            }
+            ora_first_derivative(g, so, periodic, a, tmp, dtmp);
+            for (size_t p = 0; p < N; ++p) hz[p] += dtmp[p];
+        }
+        if (lq) {
+            /* lq += D_a (D_a q) */
+            ora_first_derivative(g, so, periodic, a, grad[a], dtmp);
+            for (size_t p = 0; p < N; ++p) lq[p] += dtmp[p];
+        }
+    }
+done:
+    for (int a = 0; a < 3; ++a) free(grad[a]);
+    free(proj);
+    free(tmp);
+    free(dtmp);
+    return st;
+}
+
+/*
+ * TTI forward model (two coupled fields p, r).  Per shot and step n:
+ *   Hxy p = L p - Hz p;
+ *   m p_tt + damp p_t = (1+2 eps) Hxy p + sqrt(1+2 delta) Hz r
+ *   m r_tt + damp r_t = sqrt(1+2 delta) Hxy p + Hz r
+ * each advanced with the same centred leapfrog as the acoustic case; src[n]
+ * is injected into p^{n+1} and r^{n+1}; rec[n] = interp(p^n).
+ * Fields eps, delta, theta, phi are [nz][ny][nx].  p_init/r_init and
+ * p_final/r_final are [nshots][2][nz][ny][nx] (levels n, n-1) or NULL.
+ */
+int ora_tti_forward(const ora_grid *g, int so, int periodic, double dt, int nt, int nshots,
+                    const float *m32, const float *damp32, const float *eps32,
+                    const float *delta32, const float *theta32, const float *phi32, int nsrc,
+                    const float *src_xyz, const float *src_wav, int nrec, const float *rec_xyz,
+                    double *rec_out, const float *p_init, const float *r_init, double *p_final,
+                    double *r_final) {
+    if (radius_of(so) < 0 || nt < 1 || nshots < 1 || nsrc < 0 || nrec < 0) return ORA_ERR_ARG;
+    const size_t N = npts(g);
+    for (int s = 0; s < nshots; ++s) {
+        if (check_sparse(g, nsrc, src_xyz + (size_t)s * nsrc * 3)) return ORA_ERR_COORD;
+        if (check_sparse(g, nrec, rec_xyz + (size_t)s * nrec * 3)) return ORA_ERR_COORD;
+    }
+    int st = ORA_OK;
+    double *m = widen(m32, N), *eps = widen(eps32, N), *del = widen(delta32, N);
+    double *th = widen(theta32, N), *ph = widen(phi32, N);
+    double *damp = damp32 ? widen(damp32, (size_t)g->nx + g->ny + g->nz) : NULL;
+    double *scale = (double *)malloc(N * sizeof(double));
+    double *bufs[10];
+    for (int b = 0; b < 10; ++b) bufs[b] = (double *)malloc(N * sizeof(double));
+    double *q = (double *)malloc(((size_t)nsrc + 1) * sizeof(double));
+    double *p = bufs[0], *pm = bufs[1], *pn = bufs[2], *r = bufs[3], *rm = bufs[4], *rn = bufs[5];
+    double *hzp = bufs[6], *lp = bufs[7], *hzr = bufs[8], *rhs = bufs[9];
+    int ok = m && eps && del && th && ph && (!damp32 || damp) && scale && q;
+    for (int b = 0; b < 10; ++b) ok = ok && bufs[b];
+    if (!ok) {
+        st = ORA_ERR_OOM;
+        goto done;
+    }
+    injection_scale(g, dt, m, damp, scale);
+    for (int s = 0; s < nshots; ++s) {
+        const float *sxyz = src_xyz + (size_t)s * nsrc * 3;
+        const float *rxyz = rec_xyz + (size_t)s * nrec * 3;
+        double *rec = rec_out ? rec_out + (size_t)s * nt * nrec : NULL;
+        for (size_t i = 0; i < N; ++i) {
+            p[i] = p_init ? (double)p_init[((size_t)s * 2 + 0) * N + i] : 0.0;
+            pm[i] = p_init ? (double)p_init[((size_t)s * 2 + 1) * N + i] : 0.0;
+            r[i] = r_init ? (double)r_init[((size_t)s * 2 + 0) * N + i] : 0.0;
+            rm[i] = r_init ? (double)r_init[((size_t)s * 2 + 1) * N + i] : 0.0;
+        }
+        for (int n = 0; n + 1 < nt; ++n) {
+            st = ora_tti_operators(g, so, periodic, th, ph, p, hzp, lp);
+            if (!st) st = ora_tti_operators(g, so, periodic, th, ph, r, hzr, NULL);
+            if (st) goto done;
+            /* p equation: rhs = (1+2eps)(Lp - Hz p) + sqrt(1+2delta) Hz r */
+            for (size_t i = 0; i < N; ++i)
+                rhs[i] = (1.0 + 2.0 * eps[i]) * (lp[i] - hzp[i]) + sqrt(1.0 + 2.0 * del[i]) * hzr[i];
+            leapfrog(g, dt, m, damp, rhs, p, pm, pn);
+            /* r equation: rhs = sqrt(1+2delta)(Lp - Hz p) + Hz r */
+            for (size_t i = 0; i < N; ++i)
+                rhs[i] = sqrt(1.0 + 2.0 * del[i]) * (lp[i] - hzp[i]) + hzr[i];
+            leapfrog(g, dt, m, damp, rhs, r, rm, rn);
+            for (int k = 0; k < nsrc; ++k) q[k] = (double)src_wav[((size_t)s * nt + n) * nsrc + k];
+            ora_inject(g, nsrc, sxyz, q, scale, pn);
+            ora_inject(g, nsrc, sxyz, q, scale, rn);
+            if (rec) ora_interpolate(g, nrec, rxyz, p, rec + (size_t)n * nrec);
+            double *t = pm;
+            pm = p;
+            p = pn;
+            pn = t;
+            t = rm;
+            rm = r;
+            r = rn;
+            rn = t;
+        }
+        if (rec) ora_interpolate(g, nrec, rxyz, p, rec + (size_t)(nt - 1) * nrec);
+        if (p_final) {
+            memcpy(p_final + ((size_t)s * 2 + 0) * N, p, N * sizeof(double));
+            memcpy(p_final + ((size_t)s * 2 + 1) * N, pm, N * sizeof(double));
+        }
+        if (r_final) {
+            memcpy(r_final + ((size_t)s * 2 + 0) * N, r, N * sizeof(double));
+            memcpy(r_final + ((size_t)s * 2 + 1) * N, rm, N * sizeof(double));
+        }
+    }
+done:
+    free(m);
+    free(eps);
+    free(del);
+    free(th);
+    free(ph);
+    free(damp);
+    free(scale);
+    free(q);
+    for (int b = 0; b < 10; ++b) free(bufs[b]);
+    return st;
+}
