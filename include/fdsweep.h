@@ -1,0 +1,164 @@
+/*
+ * fdsweep.h -- C ABI of the GB300 (sm_103a) finite-difference wave-propagation
+ * sweep: the time-stepped 3-D stencil operators of arXiv:1807.03032 (Devito),
+ * isotropic acoustic and TTI, with sparse source injection and receiver
+ * interpolation.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - Arrays are C order [z][y][x] (x fastest).  Grid index (i, j, k) sits at
+ *    coordinate (ox + i hx, oy + j hy, oz + k hz).  The grid shape includes
+ *    the absorbing border ("Domain" region of the paper's section "Domain,
+ *    halo, and padding regions"); points outside it are zero ghosts.
+ *  - Units: m, ms, km/s (= m/ms); m = 1/v^2 in ms^2/m^2.
+ *  - so (space order) is one of 2, 4, 8, 12, 16; the stencil radius is so/2.
+ *  - Every pointer may be device memory or host memory (pinned or pageable);
+ *    the library detects which with cudaPointerGetAttributes and copies host
+ *    data through its own device workspace.  Pointers are owned by the
+ *    caller; the library never frees or retains them.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = the legacy default
+ *    stream).  The library allocates its workspace with cudaMallocAsync on
+ *    that stream and frees it before returning.  Each call synchronises the
+ *    stream once, at its end, to report device-side errors; when it returns
+ *    FD_OK all outputs are complete.
+ *  - Errors: a negative fd_status; fd_last_error() returns a message for the
+ *    calling thread.  Outputs are unspecified after an error.  Arguments are
+ *    validated before any launch: bad sizes or null required pointers give
+ *    FD_ERR_ARG, an unsupported space order FD_ERR_SO, a time step above the
+ *    stability bound FD_ERR_CFL, a sparse point outside the grid
+ *    FD_ERR_COORD, a failed allocation FD_ERR_OOM, a non-finite final field
+ *    FD_ERR_DIVERGED, any CUDA failure FD_ERR_CUDA, a device-side wait that
+ *    ran out FD_ERR_TIMEOUT.
+ *  - Shots are the outermost dimension of per-shot arrays; all shots share
+ *    the medium (m, damp and the TTI fields).
+ */
+#ifndef FDSWEEP_H
+#define FDSWEEP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Grid descriptor (the paper's Grid(shape, extent, origin), section
+ * "Symbolic types"). */
+typedef struct {
+    int32_t nx, ny, nz; /* points per axis, including the absorbing border */
+    double hx, hy, hz;  /* spacing [m] */
+    double ox, oy, oz;  /* origin [m] */
+} fd_grid;
+
+typedef enum {
+    FD_OK = 0,
+    FD_ERR_ARG = -1,
+    FD_ERR_CFL = -2,
+    FD_ERR_SO = -3,
+    FD_ERR_COORD = -4,
+    FD_ERR_OOM = -5,
+    FD_ERR_CUDA = -6,
+    FD_ERR_DIVERGED = -7,
+    FD_ERR_UNIMPL = -8,
+    FD_ERR_TIMEOUT = -9
+} fd_status;
+
+/*
+ * acoustic_forward -- isotropic acoustic forward model.
+ *
+ * Solves m u_tt + damp u_t - lap(u) = src (Eq. WE with an absorbing term)
+ * with the explicit leapfrog of Listing fd-3, central compact Laplacian of
+ * order `so` (Listing fd-1/fd-2), damping discretised centrally:
+ *   u^{n+1} = (dt^2 lap u^n + m (2u^n - u^{n-1}) + eta u^{n-1}) / (m + eta),
+ *   eta = damp dt / 2.
+ * Per step n = 0..nt-2: stencil update; then source samples src_wav[n] are
+ * injected into u^{n+1} with trilinear weights w_c and scale
+ * dt^2 / (m + eta) at each node (Eq. interp, Listing finject); receivers
+ * record rec[n] = sum_c w_c u^n(node_c).  Finally rec[nt-1] samples u^{nt-1}.
+ * Interpolation index x1 = floor((x - o)/h) (FP64), clamped to n-2.
+ *
+ *   grid      shape/spacing/origin; nx, ny, nz > so.
+ *   so        space order (2, 4, 8, 12, 16).
+ *   dt        time step [ms]; must satisfy the leapfrog stability bound
+ *             dt <= 2 / (v_max sqrt(sum_d sigma/h_d^2)), v_max = 1/sqrt(min m),
+ *             sigma = max of the stencil's symbol (else FD_ERR_CFL).
+ *   nt        number of time samples (>= 1); nt-1 steps are taken.
+ *   nshots    independent shots sharing the medium (>= 1).
+ *   m         [nz][ny][nx] squared slowness, finite and > 0.
+ *   damp      NULL (no damping) or [nx + ny + nz]: per-axis profiles
+ *             (x block, then y, then z); damp(i,j,k) = dx[i] + dy[j] + dz[k],
+ *             finite and >= 0.
+ *   nsrc, src_xyz [nshots][nsrc][3], src_wav [nshots][nt][nsrc]: sources.
+ *   nrec, rec_xyz [nshots][nrec][3]: receivers; rec_out [nshots][nt][nrec]
+ *             (may be NULL when nrec = 0).
+ *   u_init    NULL (zero initial state, Eq. WE) or [nshots][2][nz][ny][nx]
+ *             holding (u^0, u^{-1}).
+ *   u_final   NULL or [nshots][2][nz][ny][nx] receiving (u^{nt-1}, u^{nt-2}).
+ *   stream    cudaStream_t to run on.
+ */
+fd_status acoustic_forward(const fd_grid *grid, int so, double dt, int nt, int nshots,
+                           const float *m, const float *damp, int nsrc, const float *src_xyz,
+                           const float *src_wav, int nrec, const float *rec_xyz, float *rec_out,
+                           const float *u_init, float *u_final, void *stream);
+
+/*
+ * tti_forward -- tilted transverse isotropy (TTI) forward model.
+ *
+ * Two coupled acoustic equations whose Laplacians are built from rotated
+ * first-derivative operators (section "Test case setup"):
+ *   Hz q  = sum_i D_i( n_i sum_j n_j D_j q ),  L q = sum_i D_i D_i q,
+ *   Hxy q = L q - Hz q,  n = (sin(theta) cos(phi), sin(theta) sin(phi), cos(theta)),
+ *   m p_tt + damp p_t = (1 + 2 eps) Hxy p + sqrt(1 + 2 delta) Hz r,
+ *   m r_tt + damp r_t = sqrt(1 + 2 delta) Hxy p + Hz r,
+ * D_i the central first derivative of order so along axis i (zero ghosts
+ * outside the grid, also for the intermediate D_j q terms).  Each equation is
+ * advanced with the same centred leapfrog as acoustic_forward; the source is
+ * injected into p and r with the same scale; receivers record p.
+ *
+ *   epsilon, delta, theta, phi  [nz][ny][nx]; eps >= delta >= -1/2 pointwise
+ *             (otherwise the system is not hyperbolic: FD_ERR_ARG).
+ *   dt        must satisfy dt <= 2 / sqrt(max(1+2eps) v_max^2 sum_d s/h_d^2),
+ *             s = max of the squared first-derivative symbol (else FD_ERR_CFL).
+ *   p_init, r_init  NULL or [nshots][2][nz][ny][nx] (levels n, n-1).
+ *   p_final, r_final NULL or [nshots][2][nz][ny][nx].
+ *   rec_out   [nshots][nt][nrec] samples of p.
+ *   Other arguments as for acoustic_forward.
+ */
+fd_status tti_forward(const fd_grid *grid, int so, double dt, int nt, int nshots, const float *m,
+                      const float *damp, const float *epsilon, const float *delta,
+                      const float *theta, const float *phi, int nsrc, const float *src_xyz,
+                      const float *src_wav, int nrec, const float *rec_xyz, float *rec_out,
+                      const float *p_init, const float *r_init, float *p_final, float *r_final,
+                      void *stream);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char *fd_last_error(void);
+
+/* Library version string. */
+const char *fd_version(void);
+
+/*
+ * Kernel timing statistics.  When enabled (fd_stats_enable(1)), the forward
+ * entry points launch their time loop without CUDA graphs and bracket every
+ * stencil-kernel launch with CUDA events on the call's stream; the elapsed
+ * times are accumulated per kernel family when the call completes.
+ * Families: "acoustic_step", "tti_pass1", "tti_pass2", "sparse".
+ * fd_stats_get returns FD_ERR_ARG for an unknown family.
+ */
+fd_status fd_stats_enable(int on);
+fd_status fd_stats_reset(void);
+fd_status fd_stats_get(const char *family, double *total_ms, int64_t *launches,
+                       double *points_per_launch);
+
+/*
+ * Tile configuration override for the acoustic stencil kernel (for tuning
+ * sweeps): index into the compiled configuration table for the given space
+ * order, or -1 for the built-in choice.  Returns FD_ERR_ARG if out of range.
+ */
+fd_status fd_set_acoustic_config(int so, int config);
+int fd_num_acoustic_configs(int so);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDSWEEP_H */

@@ -1,0 +1,124 @@
+"""ctypes binding of libfdsweep.so (the C ABI declared in include/fdsweep.h).
+
+Argument marshalling only: every step of the sweep runs in the library's CUDA
+kernels.  There is no fallback: if the library has not been built (run
+``python -m paper_1807_03032_gb300.build`` or ``__graft_entry__.build()``) or
+cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libfdsweep.so")
+
+FD_OK = 0
+STATUS_NAMES = {
+    0: "FD_OK", -1: "FD_ERR_ARG", -2: "FD_ERR_CFL", -3: "FD_ERR_SO", -4: "FD_ERR_COORD",
+    -5: "FD_ERR_OOM", -6: "FD_ERR_CUDA", -7: "FD_ERR_DIVERGED", -8: "FD_ERR_UNIMPL",
+    -9: "FD_ERR_TIMEOUT",
+}
+
+# Every symbol include/fdsweep.h declares (checked by the ABI test).
+EXPORTED = ("acoustic_forward", "tti_forward", "fd_last_error", "fd_version",
+            "fd_stats_enable", "fd_stats_reset", "fd_stats_get", "fd_set_acoustic_config",
+            "fd_num_acoustic_configs")
+
+
+class FdGrid(ctypes.Structure):
+    """Mirror of fd_grid."""
+
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("hx", ctypes.c_double), ("hy", ctypes.c_double), ("hz", ctypes.c_double),
+                ("ox", ctypes.c_double), ("oy", ctypes.c_double), ("oz", ctypes.c_double)]
+
+
+class FdError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        self.name = STATUS_NAMES.get(status, str(status))
+        super().__init__(f"{self.name}: {message}")
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libfdsweep.so and declare the ABI; raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"libfdsweep.so not found at {path}: build the CUDA library first "
+                "(python -m paper_1807_03032_gb300.build)")
+        lib = ctypes.CDLL(path)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        G = ctypes.POINTER(FdGrid)
+        lib.acoustic_forward.argtypes = [G, I, D, I, I, P, P, I, P, P, I, P, P, P, P, P]
+        lib.acoustic_forward.restype = I
+        lib.tti_forward.argtypes = [G, I, D, I, I, P, P, P, P, P, P, I, P, P, I, P, P, P, P, P,
+                                    P, P]
+        lib.tti_forward.restype = I
+        lib.fd_last_error.argtypes = []
+        lib.fd_last_error.restype = ctypes.c_char_p
+        lib.fd_version.argtypes = []
+        lib.fd_version.restype = ctypes.c_char_p
+        lib.fd_stats_enable.argtypes = [I]
+        lib.fd_stats_enable.restype = I
+        lib.fd_stats_reset.argtypes = []
+        lib.fd_stats_reset.restype = I
+        lib.fd_stats_get.argtypes = [ctypes.c_char_p, ctypes.POINTER(D),
+                                     ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D)]
+        lib.fd_stats_get.restype = I
+        lib.fd_set_acoustic_config.argtypes = [I, I]
+        lib.fd_set_acoustic_config.restype = I
+        lib.fd_num_acoustic_configs.argtypes = [I]
+        lib.fd_num_acoustic_configs.restype = I
+        _lib = lib
+        return lib
+
+
+def check(status: int):
+    if status != FD_OK:
+        msg = load().fd_last_error().decode(errors="replace")
+        raise FdError(status, msg)
+
+
+def grid_struct(shape_zyx, spacing_xyz, origin_xyz=(0.0, 0.0, 0.0)) -> FdGrid:
+    nz, ny, nx = (int(v) for v in shape_zyx)
+    return FdGrid(nx, ny, nz, *(float(v) for v in spacing_xyz), *(float(v) for v in origin_xyz))
+
+
+def version() -> str:
+    return load().fd_version().decode()
+
+
+def stats_enable(on: bool = True):
+    check(load().fd_stats_enable(1 if on else 0))
+
+
+def stats_reset():
+    check(load().fd_stats_reset())
+
+
+def stats_get(family: str):
+    """(total_ms, launches, points_per_launch) accumulated for a kernel family."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    pts = ctypes.c_double()
+    check(load().fd_stats_get(family.encode(), ctypes.byref(ms), ctypes.byref(n),
+                              ctypes.byref(pts)))
+    return ms.value, n.value, pts.value
+
+
+def set_acoustic_config(so: int, config: int):
+    check(load().fd_set_acoustic_config(int(so), int(config)))
+
+
+def num_acoustic_configs(so: int) -> int:
+    return int(load().fd_num_acoustic_configs(int(so)))

@@ -1,0 +1,686 @@
+// api.cu -- the C-ABI entry points (include/fdsweep.h): argument validation,
+// stability check, workspace, coefficient setup and the time loop.
+//
+// Per time step n (the paper's schedule of one time iteration: stencil
+// update, then sparse injection into the t+1 field; receivers sample t):
+//   acoustic:  K1 acoustic_step  ->  K3/K4 sparse (inject src[n] into u^{n+1},
+//              interpolate rec[n] from u^n)
+//   TTI:       K2a tti_pass1 -> K2b tti_pass2 -> K3/K4 sparse
+// Steps are captured into a CUDA graph of kGraphChunk steps that is replayed;
+// the sparse kernel reads its time index from a device counter that the
+// graph's last node advances.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "kernels.cuh"
+#include "runtime.cuh"
+
+namespace fdsweep {
+
+fd_status finish_medium_stats(MediumStats *dev_stats, cudaStream_t stream);
+
+namespace {
+
+constexpr int kGraphChunk = 16;  // steps per captured graph (even: parity repeats)
+
+// Central FD weights for radius r, closed form:
+//   second derivative w_k = 2 (-1)^{k+1} (r!)^2 / (k^2 (r-k)! (r+k)!), w_0 = -2 sum w_k
+//   first derivative  c_k = (-1)^{k+1} (r!)^2 / (k (r-k)! (r+k)!)
+void fd_weights(int r, double *w, double *c) {
+    double ratio = 1.0, sum = 0.0;
+    w[0] = 0.0;
+    c[0] = 0.0;
+    for (int k = 1; k <= r; ++k) {
+        ratio = ratio * (double)(r - k + 1) / (double)(r + k);
+        const double sign = (k & 1) ? 1.0 : -1.0;
+        w[k] = 2.0 * sign * ratio / ((double)k * k);
+        c[k] = sign * ratio / (double)k;
+        sum += w[k];
+    }
+    w[0] = -2.0 * sum;
+}
+
+// max over theta of the second-derivative symbol -(w0 + 2 sum w_k cos k theta)
+double second_symbol_max(int r, const double *w) {
+    double best = 0.0;
+    for (int t = 0; t <= 4096; ++t) {
+        const double th = M_PI * t / 4096.0;
+        double s = w[0];
+        for (int k = 1; k <= r; ++k) s += 2.0 * w[k] * cos(k * th);
+        if (-s > best) best = -s;
+    }
+    return best;
+}
+
+// max over theta of the squared first-derivative symbol (2 sum c_k sin k theta)^2
+double first_symbol_sq_max(int r, const double *c) {
+    double best = 0.0;
+    for (int t = 0; t <= 4096; ++t) {
+        const double th = M_PI * t / 4096.0;
+        double s = 0.0;
+        for (int k = 1; k <= r; ++k) s += 2.0 * c[k] * sin(k * th);
+        if (s * s > best) best = s * s;
+    }
+    return best;
+}
+
+bool valid_so(int so) { return so == 2 || so == 4 || so == 8 || so == 12 || so == 16; }
+
+int g_acoustic_config[kMaxRadius + 1] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
+
+fd_status validate_common(const fd_grid *g, int so, double dt, int nt, int nshots, const float *m,
+                          int nsrc, const float *src_xyz, const float *src_wav, int nrec,
+                          const float *rec_xyz, const float *rec_out) {
+    if (!g) return set_error(FD_ERR_ARG, "grid is null");
+    if (!valid_so(so)) return set_error(FD_ERR_SO, "space order %d not in {2,4,8,12,16}", so);
+    if (g->nx < 2 || g->ny < 2 || g->nz < 2)
+        return set_error(FD_ERR_ARG, "grid shape %d x %d x %d: every axis needs >= 2 points",
+                         g->nx, g->ny, g->nz);
+    const double hs[3] = {g->hx, g->hy, g->hz}, os[3] = {g->ox, g->oy, g->oz};
+    for (int a = 0; a < 3; ++a) {
+        if (!(hs[a] > 0.0) || !isfinite(hs[a]))
+            return set_error(FD_ERR_ARG, "grid spacing must be finite and > 0");
+        if (!isfinite(os[a])) return set_error(FD_ERR_ARG, "grid origin must be finite");
+    }
+    const int64_t nxp = (g->nx + 3) / 4 * 4;
+    const int64_t vol = nxp * g->ny * (int64_t)g->nz;
+    if (vol >= (int64_t)1 << 32)
+        return set_error(FD_ERR_ARG, "grid of %lld padded points exceeds 2^32", (long long)vol);
+    if (!(dt > 0.0) || !isfinite(dt)) return set_error(FD_ERR_ARG, "dt must be finite and > 0");
+    if (nt < 1) return set_error(FD_ERR_ARG, "nt must be >= 1");
+    if (nshots < 1) return set_error(FD_ERR_ARG, "nshots must be >= 1");
+    if (!m) return set_error(FD_ERR_ARG, "m is null");
+    if (nsrc < 0 || nrec < 0) return set_error(FD_ERR_ARG, "nsrc and nrec must be >= 0");
+    if (nsrc > 0 && (!src_xyz || !src_wav))
+        return set_error(FD_ERR_ARG, "sources given but src_xyz or src_wav is null");
+    if (nrec > 0 && (!rec_xyz || !rec_out))
+        return set_error(FD_ERR_ARG, "receivers given but rec_xyz or rec_out is null");
+    return FD_OK;
+}
+
+// An input array that may live on the host: device copy in the workspace.
+struct Staged {
+    const float *user = nullptr;
+    size_t count = 0;
+    bool host = false;
+    float *dev = nullptr;
+    void plan(Workspace &ws, const float *p, size_t n) {
+        user = p;
+        count = n;
+        host = p && n && !is_device_pointer(p);
+        if (host) ws.reserve(n * sizeof(float));
+    }
+    fd_status place(Workspace &ws, cudaStream_t s) {
+        if (!user || !count) return FD_OK;
+        if (!host) {
+            dev = const_cast<float *>(user);
+            return FD_OK;
+        }
+        dev = ws.take_n<float>(count);
+        FD_CUDA_TRY(cudaMemcpyAsync(dev, user, count * sizeof(float), cudaMemcpyHostToDevice, s));
+        return FD_OK;
+    }
+};
+
+// An output array that may live on the host: written in the workspace, copied
+// back at the end.
+struct StagedOut {
+    float *user = nullptr;
+    size_t count = 0;
+    bool host = false;
+    float *dev = nullptr;
+    void plan(Workspace &ws, float *p, size_t n) {
+        user = p;
+        count = n;
+        host = p && n && !is_device_pointer(p);
+        if (host) ws.reserve(n * sizeof(float));
+    }
+    void place(Workspace &ws) {
+        if (!user || !count) return;
+        dev = host ? ws.take_n<float>(count) : user;
+    }
+    fd_status copy_back(cudaStream_t s) {
+        if (host && count)
+            FD_CUDA_TRY(cudaMemcpyAsync(user, dev, count * sizeof(float), cudaMemcpyDeviceToHost, s));
+        return FD_OK;
+    }
+};
+
+// Host copy of the device MediumStats after a synchronisation.
+fd_status read_stats(const MediumStats *dev, MediumStats *host, cudaStream_t s) {
+    FD_CUDA_TRY(cudaMemcpyAsync(host, dev, sizeof(MediumStats), cudaMemcpyDeviceToHost, s));
+    FD_CUDA_TRY(cudaStreamSynchronize(s));
+    return FD_OK;
+}
+
+fd_status flags_to_status(unsigned int flags, const char *what) {
+    if (flags & DEV_ERR_TIMEOUT)
+        return set_error(FD_ERR_TIMEOUT, "%s: a device-side wait ran out (kernel aborted)", what);
+    if (flags & DEV_ERR_COORD)
+        return set_error(FD_ERR_COORD, "%s: a source or receiver lies outside the grid", what);
+    if (flags & DEV_ERR_MEDIUM)
+        return set_error(FD_ERR_ARG,
+                         "%s: medium out of range (need finite m > 0, damp >= 0; TTI: "
+                         "eps >= delta, 1 + 2 delta >= 0, finite angles)",
+                         what);
+    if (flags & DEV_ERR_NONFINITE)
+        return set_error(FD_ERR_DIVERGED, "%s: the wavefield became non-finite", what);
+    return FD_OK;
+}
+
+// Copies nfields dense [nz][ny][nx] arrays into (or out of) padded buffers.
+fd_status copy_fields_in(float *dst_base, const WaveLayout &L, const float *src, int shot,
+                         int nlev, int fields_per_shot, int first_level, cudaStream_t s) {
+    const size_t dense = (size_t)L.nx * L.ny * L.nz;
+    for (int l = 0; l < nlev; ++l) {
+        float *dst = dst_base + (int64_t)(shot * fields_per_shot + first_level + l) * L.vol;
+        const float *sp = src + ((size_t)shot * nlev + l) * dense;
+        FD_CUDA_TRY(cudaMemcpy2DAsync(dst, (size_t)L.nxp * 4, sp, (size_t)L.nx * 4,
+                                      (size_t)L.nx * 4, (size_t)L.ny * L.nz, cudaMemcpyDefault,
+                                      s));
+    }
+    return FD_OK;
+}
+
+fd_status copy_field_out(float *dst_dense, const float *src_buf, const WaveLayout &L,
+                         cudaStream_t s) {
+    FD_CUDA_TRY(cudaMemcpy2DAsync(dst_dense, (size_t)L.nx * 4, src_buf, (size_t)L.nxp * 4,
+                                  (size_t)L.nx * 4, (size_t)L.ny * L.nz, cudaMemcpyDefault, s));
+    return FD_OK;
+}
+
+// Runs `nsteps` steps.  step(i, parity, use_counter) enqueues one step; with
+// use_counter the sparse kernel's time index is *counter + i, otherwise i.
+template <class StepFn>
+fd_status run_time_loop(int nsteps, cudaStream_t s, int *counter, bool allow_graph,
+                        StepFn step) {
+    int n = 0;
+    if (allow_graph && nsteps >= 2 * kGraphChunk) {
+        FD_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            fd_status st = FD_OK;
+            for (int i = 0; i < kGraphChunk && st == FD_OK; ++i) st = step(i, i & 1, true);
+            if (st == FD_OK) st = bump_counter(counter, kGraphChunk, s);
+            cudaError_t e = cudaStreamEndCapture(s, &graph);
+            if (st != FD_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            FD_CUDA_TRY(e);
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            FD_CUDA_TRY(e);
+            const int reps = nsteps / kGraphChunk;
+            for (int r = 0; r < reps; ++r) {
+                e = cudaGraphLaunch(exec, s);
+                if (e != cudaSuccess) break;
+            }
+            cudaGraphExecDestroy(exec);  // released once the queued launches complete
+            FD_CUDA_TRY(e);
+            n = reps * kGraphChunk;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    for (; n < nsteps; ++n) FD_TRY(step(n, n & 1, false));
+    return FD_OK;
+}
+
+// Events bracketing the kernels of every step when statistics are on.
+struct StepEvents {
+    std::vector<cudaEvent_t> ev;
+    int per_step = 0;
+    ~StepEvents() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+    fd_status create(int nsteps, int per) {
+        per_step = per;
+        ev.assign((size_t)nsteps * per, nullptr);
+        for (auto &e : ev) FD_CUDA_TRY(cudaEventCreate(&e));
+        return FD_OK;
+    }
+    cudaEvent_t at(int step, int k) { return ev[(size_t)step * per_step + k]; }
+    double elapsed(int step, int k0, int k1) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, at(step, k0), at(step, k1));
+        return ms;
+    }
+};
+
+struct GridDerived {
+    WaveLayout L;
+    double w[kMaxRadius + 1], c[kMaxRadius + 1];
+};
+
+GridDerived derive(const fd_grid *g, int so) {
+    GridDerived d;
+    d.L.nx = g->nx;
+    d.L.ny = g->ny;
+    d.L.nz = g->nz;
+    d.L.nxp = (g->nx + 3) / 4 * 4;
+    d.L.plane = (int64_t)d.L.nxp * g->ny;
+    d.L.vol = d.L.plane * g->nz;
+    for (int k = 0; k <= kMaxRadius; ++k) d.w[k] = d.c[k] = 0.0;
+    fd_weights(so / 2, d.w, d.c);
+    return d;
+}
+
+}  // namespace
+
+// ====================================================================== acoustic
+
+static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, int nt, int nshots,
+                                       const float *m, const float *damp, int nsrc,
+                                       const float *src_xyz, const float *src_wav, int nrec,
+                                       const float *rec_xyz, float *rec_out, const float *u_init,
+                                       float *u_final, cudaStream_t caller) {
+    FD_TRY(validate_common(grid, so, dt, nt, nshots, m, nsrc, src_xyz, src_wav, nrec, rec_xyz,
+                           rec_out));
+    const int R = so / 2;
+    GridDerived gd = derive(grid, so);
+    const WaveLayout &L = gd.L;
+    const size_t dense = (size_t)L.nx * L.ny * L.nz;
+    const int ndamp = L.nx + L.ny + L.nz;
+
+    CallStream cs;
+    FD_TRY(cs.begin(caller));
+    cudaStream_t s = cs.get();
+
+    Workspace ws;
+    ws.reserve((size_t)2 * nshots * L.vol * 4);        // wavefields
+    ws.reserve((size_t)L.vol * 4);                      // b
+    ws.reserve((size_t)ndamp * 4);                      // damping / dt
+    ws.reserve((size_t)nshots * nsrc * sizeof(SparsePoint));
+    ws.reserve((size_t)nshots * nrec * sizeof(SparsePoint));
+    ws.reserve(sizeof(MediumStats) + 64);
+    Staged sm, sdamp, ssxyz, swav, srxyz;
+    StagedOut srec;
+    sm.plan(ws, m, dense);
+    sdamp.plan(ws, damp, damp ? ndamp : 0);
+    ssxyz.plan(ws, src_xyz, (size_t)nshots * nsrc * 3);
+    swav.plan(ws, src_wav, (size_t)nshots * nt * nsrc);
+    srxyz.plan(ws, rec_xyz, (size_t)nshots * nrec * 3);
+    srec.plan(ws, rec_out, (size_t)nshots * nt * nrec);
+    FD_TRY(ws.allocate(s));
+
+    float *wave = ws.take_n<float>((size_t)2 * nshots * L.vol);
+    float *bcoef = ws.take_n<float>(L.vol);
+    float *dps = ws.take_n<float>(ndamp);
+    SparsePoint *src_tab = ws.take_n<SparsePoint>((size_t)nshots * nsrc + 1);
+    SparsePoint *rec_tab = ws.take_n<SparsePoint>((size_t)nshots * nrec + 1);
+    MediumStats *dstats = static_cast<MediumStats *>(ws.take(sizeof(MediumStats)));
+    int *counter = static_cast<int *>(ws.take(64));
+    FD_TRY(sm.place(ws, s));
+    FD_TRY(sdamp.place(ws, s));
+    FD_TRY(ssxyz.place(ws, s));
+    FD_TRY(swav.place(ws, s));
+    FD_TRY(srxyz.place(ws, s));
+    srec.place(ws);
+
+    // ---- K0: coefficients, tables, validation
+    FD_CUDA_TRY(cudaMemsetAsync(bcoef, 0, (size_t)L.vol * 4, s));
+    FD_TRY(init_medium_stats(dstats, s));
+    FD_TRY(setup_acoustic_coeffs(sm.dev, sdamp.dev, dt, L, bcoef, dps, dstats, s));
+    for (int sh = 0; sh < nshots; ++sh) {
+        FD_TRY(setup_sparse_table(ssxyz.dev ? ssxyz.dev + (size_t)sh * nsrc * 3 : nullptr, nsrc,
+                                  *grid, L, src_tab + (size_t)sh * nsrc, &dstats->flags, s));
+        FD_TRY(setup_sparse_table(srxyz.dev ? srxyz.dev + (size_t)sh * nrec * 3 : nullptr, nrec,
+                                  *grid, L, rec_tab + (size_t)sh * nrec, &dstats->flags, s));
+    }
+    FD_TRY(finish_medium_stats(dstats, s));
+    MediumStats hs;
+    FD_TRY(read_stats(dstats, &hs, s));
+    FD_TRY(flags_to_status(hs.flags, "acoustic_forward"));
+    {
+        const double vmax = 1.0 / sqrt((double)hs.m_min);
+        const double sig = second_symbol_max(R, gd.w);
+        const double lam = sig * (1.0 / (grid->hx * grid->hx) + 1.0 / (grid->hy * grid->hy) +
+                                  1.0 / (grid->hz * grid->hz));
+        const double dt_max = 2.0 / (vmax * sqrt(lam));
+        if (dt > dt_max * (1.0 + 1e-12))
+            return set_error(FD_ERR_CFL,
+                             "dt = %.6g ms exceeds the leapfrog stability bound %.6g ms "
+                             "(v_max = %.6g km/s, so = %d)",
+                             dt, dt_max, vmax, so);
+    }
+
+    // ---- initial state
+    FD_CUDA_TRY(cudaMemsetAsync(wave, 0, (size_t)2 * nshots * L.vol * 4, s));
+    if (u_init)
+        for (int sh = 0; sh < nshots; ++sh) FD_TRY(copy_fields_in(wave, L, u_init, sh, 2, 2, 0, s));
+
+    // ---- K1 plan and arguments
+    AcousticPlan plan;
+    FD_TRY(acoustic_plan(R, g_acoustic_config[R], L, nshots, wave, &plan));
+    AcousticStepArgs a;
+    memset(&a, 0, sizeof(a));
+    a.wave = wave;
+    a.bcoef = bcoef;
+    a.dpx = dps;
+    a.dpy = dps + L.nx;
+    a.dpz = dps + L.nx + L.ny;
+    a.L = L;
+    a.nshots = nshots;
+    a.err = &dstats->flags;
+    const double ih2[3] = {1.0 / (grid->hx * grid->hx), 1.0 / (grid->hy * grid->hy),
+                           1.0 / (grid->hz * grid->hz)};
+    a.wc = (float)(gd.w[0] * (ih2[0] + ih2[1] + ih2[2]));
+    for (int k = 1; k <= R; ++k) {
+        a.wx[k] = (float)(gd.w[k] * ih2[0]);
+        a.wy[k] = (float)(gd.w[k] * ih2[1]);
+        a.wz[k] = (float)(gd.w[k] * ih2[2]);
+    }
+    SparseArgs sp;
+    memset(&sp, 0, sizeof(sp));
+    sp.wave = wave;
+    sp.fields_per_shot = 2;
+    sp.L = L;
+    sp.bcoef = bcoef;
+    sp.nshots = nshots;
+    sp.nt = nt;
+    sp.nsrc = nsrc;
+    sp.src_tab = src_tab;
+    sp.src_wav = swav.dev;
+    sp.inj_level1 = -1;
+    sp.nrec = nrec;
+    sp.rec_tab = rec_tab;
+    sp.rec_out = srec.dev;
+
+    // ---- time loop
+    const int nsteps = nt - 1;
+    const bool timing = stats_enabled();
+    StepEvents evs;
+    if (timing) FD_TRY(evs.create(nsteps, 3));
+    auto step = [&](int i, int par, bool via_counter) -> fd_status {
+        AcousticStepArgs ai = a;
+        ai.cur = par;
+        if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 0), s));
+        FD_TRY(acoustic_launch(plan, ai, s));
+        if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 1), s));
+        SparseArgs si = sp;
+        si.inj_level0 = 1 - par;
+        si.rec_level = par;
+        si.step_base = via_counter ? counter : nullptr;
+        FD_TRY(sparse_launch(si, i, nsrc > 0, nrec > 0, s));
+        if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 2), s));
+        return FD_OK;
+    };
+    FD_TRY(run_time_loop(nsteps, s, counter, !timing, step));
+    const int last = nsteps & 1;  // level holding u^{nt-1}
+    {
+        SparseArgs si = sp;
+        si.rec_level = last;
+        si.step_base = nullptr;
+        FD_TRY(sparse_launch(si, nt - 1, false, nrec > 0, s));
+    }
+    FD_TRY(check_finite(wave, L, 2 * nshots, &dstats->flags, s));
+
+    // ---- outputs
+    if (u_final) {
+        for (int sh = 0; sh < nshots; ++sh) {
+            float *dst = u_final + (size_t)sh * 2 * dense;
+            FD_TRY(copy_field_out(dst, wave + (int64_t)(2 * sh + last) * L.vol, L, s));
+            FD_TRY(copy_field_out(dst + dense, wave + (int64_t)(2 * sh + 1 - last) * L.vol, L, s));
+        }
+    }
+    FD_TRY(srec.copy_back(s));
+    FD_TRY(read_stats(dstats, &hs, s));
+    if (timing && nsteps > 0) {
+        double k1 = 0.0, spm = 0.0;
+        for (int i = 0; i < nsteps; ++i) {
+            k1 += evs.elapsed(i, 0, 1);
+            spm += evs.elapsed(i, 1, 2);
+        }
+        stats_add("acoustic_step", k1, nsteps, (double)dense * nshots);
+        stats_add("sparse", spm, nsteps, (double)(nrec + 8 * nsrc) * nshots);
+    }
+    ws.release();
+    FD_TRY(cs.finish());
+    return flags_to_status(hs.flags, "acoustic_forward");
+}
+
+// ====================================================================== TTI
+
+static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt, int nshots,
+                                  const float *m, const float *damp, const float *eps,
+                                  const float *delta, const float *theta, const float *phi,
+                                  int nsrc, const float *src_xyz, const float *src_wav, int nrec,
+                                  const float *rec_xyz, float *rec_out, const float *p_init,
+                                  const float *r_init, float *p_final, float *r_final,
+                                  cudaStream_t caller) {
+    FD_TRY(validate_common(grid, so, dt, nt, nshots, m, nsrc, src_xyz, src_wav, nrec, rec_xyz,
+                           rec_out));
+    if (!eps || !delta || !theta || !phi)
+        return set_error(FD_ERR_ARG, "tti_forward: epsilon, delta, theta and phi are required");
+    const int R = so / 2;
+    GridDerived gd = derive(grid, so);
+    const WaveLayout &L = gd.L;
+    const size_t dense = (size_t)L.nx * L.ny * L.nz;
+    const int ndamp = L.nx + L.ny + L.nz;
+
+    CallStream cs;
+    FD_TRY(cs.begin(caller));
+    cudaStream_t s = cs.get();
+
+    Workspace ws;
+    ws.reserve((size_t)4 * nshots * L.vol * 4);  // p, r at two levels
+    ws.reserve((size_t)6 * nshots * L.vol * 4);  // pass-1 temporaries
+    ws.reserve((size_t)6 * L.vol * 4);           // b, a, s, n (3)
+    ws.reserve((size_t)ndamp * 4);
+    ws.reserve((size_t)nshots * nsrc * sizeof(SparsePoint));
+    ws.reserve((size_t)nshots * nrec * sizeof(SparsePoint));
+    ws.reserve(sizeof(MediumStats) + 64);
+    Staged sm, sdamp, seps, sdel, sth, sph, ssxyz, swav, srxyz;
+    StagedOut srec;
+    sm.plan(ws, m, dense);
+    sdamp.plan(ws, damp, damp ? ndamp : 0);
+    seps.plan(ws, eps, dense);
+    sdel.plan(ws, delta, dense);
+    sth.plan(ws, theta, dense);
+    sph.plan(ws, phi, dense);
+    ssxyz.plan(ws, src_xyz, (size_t)nshots * nsrc * 3);
+    swav.plan(ws, src_wav, (size_t)nshots * nt * nsrc);
+    srxyz.plan(ws, rec_xyz, (size_t)nshots * nrec * 3);
+    srec.plan(ws, rec_out, (size_t)nshots * nt * nrec);
+    FD_TRY(ws.allocate(s));
+
+    float *wave = ws.take_n<float>((size_t)4 * nshots * L.vol);
+    float *tmp = ws.take_n<float>((size_t)6 * nshots * L.vol);
+    float *bcoef = ws.take_n<float>(L.vol);
+    float *acoef = ws.take_n<float>(L.vol);
+    float *scoef = ws.take_n<float>(L.vol);
+    float *nvec = ws.take_n<float>((size_t)3 * L.vol);
+    float *dps = ws.take_n<float>(ndamp);
+    SparsePoint *src_tab = ws.take_n<SparsePoint>((size_t)nshots * nsrc + 1);
+    SparsePoint *rec_tab = ws.take_n<SparsePoint>((size_t)nshots * nrec + 1);
+    MediumStats *dstats = static_cast<MediumStats *>(ws.take(sizeof(MediumStats)));
+    int *counter = static_cast<int *>(ws.take(64));
+    for (Staged *st : {&sm, &sdamp, &seps, &sdel, &sth, &sph, &ssxyz, &swav, &srxyz})
+        FD_TRY(st->place(ws, s));
+    srec.place(ws);
+
+    FD_CUDA_TRY(cudaMemsetAsync(bcoef, 0, (size_t)6 * L.vol * 4, s));
+    FD_TRY(init_medium_stats(dstats, s));
+    FD_TRY(setup_acoustic_coeffs(sm.dev, sdamp.dev, dt, L, bcoef, dps, dstats, s));
+    FD_TRY(setup_tti_coeffs(seps.dev, sdel.dev, sth.dev, sph.dev, L, acoef, scoef, nvec, dstats,
+                            s));
+    for (int sh = 0; sh < nshots; ++sh) {
+        FD_TRY(setup_sparse_table(ssxyz.dev ? ssxyz.dev + (size_t)sh * nsrc * 3 : nullptr, nsrc,
+                                  *grid, L, src_tab + (size_t)sh * nsrc, &dstats->flags, s));
+        FD_TRY(setup_sparse_table(srxyz.dev ? srxyz.dev + (size_t)sh * nrec * 3 : nullptr, nrec,
+                                  *grid, L, rec_tab + (size_t)sh * nrec, &dstats->flags, s));
+    }
+    FD_TRY(finish_medium_stats(dstats, s));
+    MediumStats hs;
+    FD_TRY(read_stats(dstats, &hs, s));
+    FD_TRY(flags_to_status(hs.flags, "tti_forward"));
+    {
+        const double vmax = 1.0 / sqrt((double)hs.m_min);
+        const double amax = 1.0 + 2.0 * (double)(hs.eps_max > 0.f ? hs.eps_max : 0.f);
+        const double sig = first_symbol_sq_max(R, gd.c);
+        const double lam = sig * (1.0 / (grid->hx * grid->hx) + 1.0 / (grid->hy * grid->hy) +
+                                  1.0 / (grid->hz * grid->hz));
+        const double dt_max = 2.0 / sqrt(amax * vmax * vmax * lam);
+        if (dt > dt_max * (1.0 + 1e-12))
+            return set_error(FD_ERR_CFL,
+                             "dt = %.6g ms exceeds the TTI stability bound %.6g ms "
+                             "(v_max = %.6g km/s, 1+2eps_max = %.4g, so = %d)",
+                             dt, dt_max, vmax, amax, so);
+    }
+
+    FD_CUDA_TRY(cudaMemsetAsync(wave, 0, (size_t)4 * nshots * L.vol * 4, s));
+    for (int sh = 0; sh < nshots; ++sh) {
+        if (p_init) FD_TRY(copy_fields_in(wave, L, p_init, sh, 2, 4, 0, s));
+        if (r_init) FD_TRY(copy_fields_in(wave, L, r_init, sh, 2, 4, 2, s));
+    }
+
+    TtiArgs a;
+    memset(&a, 0, sizeof(a));
+    a.wave = wave;
+    a.tmp = tmp;
+    a.bcoef = bcoef;
+    a.acoef = acoef;
+    a.scoef = scoef;
+    a.nvec = nvec;
+    a.dpx = dps;
+    a.dpy = dps + L.nx;
+    a.dpz = dps + L.nx + L.ny;
+    a.L = L;
+    a.nshots = nshots;
+    a.err = &dstats->flags;
+    for (int k = 1; k <= R; ++k) {
+        a.cx[k] = (float)(gd.c[k] / grid->hx);
+        a.cy[k] = (float)(gd.c[k] / grid->hy);
+        a.cz[k] = (float)(gd.c[k] / grid->hz);
+    }
+    SparseArgs sp;
+    memset(&sp, 0, sizeof(sp));
+    sp.wave = wave;
+    sp.fields_per_shot = 4;
+    sp.L = L;
+    sp.bcoef = bcoef;
+    sp.nshots = nshots;
+    sp.nt = nt;
+    sp.nsrc = nsrc;
+    sp.src_tab = src_tab;
+    sp.src_wav = swav.dev;
+    sp.nrec = nrec;
+    sp.rec_tab = rec_tab;
+    sp.rec_out = srec.dev;
+
+    const int nsteps = nt - 1;
+    const bool timing = stats_enabled();
+    StepEvents evs;
+    if (timing) FD_TRY(evs.create(nsteps, 4));
+    auto step = [&](int i, int par, bool via_counter) -> fd_status {
+        TtiArgs ai = a;
+        ai.cur = par;
+        cudaEvent_t ev3[3];
+        if (timing)
+            for (int k = 0; k < 3; ++k) ev3[k] = evs.at(i, k);
+        FD_TRY(tti_launch(R, ai, s, nullptr, nullptr, timing ? ev3 : nullptr));
+        SparseArgs si = sp;
+        si.inj_level0 = 1 - par;
+        si.inj_level1 = 3 - par;
+        si.rec_level = par;
+        si.step_base = via_counter ? counter : nullptr;
+        FD_TRY(sparse_launch(si, i, nsrc > 0, nrec > 0, s));
+        if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 3), s));
+        return FD_OK;
+    };
+    FD_TRY(run_time_loop(nsteps, s, counter, !timing, step));
+    const int last = nsteps & 1;
+    {
+        SparseArgs si = sp;
+        si.rec_level = last;
+        si.step_base = nullptr;
+        FD_TRY(sparse_launch(si, nt - 1, false, nrec > 0, s));
+    }
+    FD_TRY(check_finite(wave, L, 4 * nshots, &dstats->flags, s));
+    for (int sh = 0; sh < nshots; ++sh) {
+        if (p_final) {
+            float *dst = p_final + (size_t)sh * 2 * dense;
+            FD_TRY(copy_field_out(dst, wave + (int64_t)(4 * sh + last) * L.vol, L, s));
+            FD_TRY(copy_field_out(dst + dense, wave + (int64_t)(4 * sh + 1 - last) * L.vol, L, s));
+        }
+        if (r_final) {
+            float *dst = r_final + (size_t)sh * 2 * dense;
+            FD_TRY(copy_field_out(dst, wave + (int64_t)(4 * sh + 2 + last) * L.vol, L, s));
+            FD_TRY(copy_field_out(dst + dense, wave + (int64_t)(4 * sh + 3 - last) * L.vol, L, s));
+        }
+    }
+    FD_TRY(srec.copy_back(s));
+    FD_TRY(read_stats(dstats, &hs, s));
+    if (timing && nsteps > 0) {
+        double t1 = 0.0, t2 = 0.0, ts = 0.0;
+        for (int i = 0; i < nsteps; ++i) {
+            t1 += evs.elapsed(i, 0, 1);
+            t2 += evs.elapsed(i, 1, 2);
+            ts += evs.elapsed(i, 2, 3);
+        }
+        stats_add("tti_pass1", t1, nsteps, (double)dense * nshots);
+        stats_add("tti_pass2", t2, nsteps, (double)dense * nshots);
+        stats_add("sparse", ts, nsteps, (double)(nrec + 16 * nsrc) * nshots);
+    }
+    ws.release();
+    FD_TRY(cs.finish());
+    return flags_to_status(hs.flags, "tti_forward");
+}
+
+}  // namespace fdsweep
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+fd_status acoustic_forward(const fd_grid *grid, int so, double dt, int nt, int nshots,
+                           const float *m, const float *damp, int nsrc, const float *src_xyz,
+                           const float *src_wav, int nrec, const float *rec_xyz, float *rec_out,
+                           const float *u_init, float *u_final, void *stream) {
+    fdsweep::clear_error();
+    return fdsweep::acoustic_forward_impl(grid, so, dt, nt, nshots, m, damp, nsrc, src_xyz,
+                                          src_wav, nrec, rec_xyz, rec_out, u_init, u_final,
+                                          static_cast<cudaStream_t>(stream));
+}
+
+fd_status tti_forward(const fd_grid *grid, int so, double dt, int nt, int nshots, const float *m,
+                      const float *damp, const float *epsilon, const float *delta,
+                      const float *theta, const float *phi, int nsrc, const float *src_xyz,
+                      const float *src_wav, int nrec, const float *rec_xyz, float *rec_out,
+                      const float *p_init, const float *r_init, float *p_final, float *r_final,
+                      void *stream) {
+    fdsweep::clear_error();
+    return fdsweep::tti_forward_impl(grid, so, dt, nt, nshots, m, damp, epsilon, delta, theta,
+                                     phi, nsrc, src_xyz, src_wav, nrec, rec_xyz, rec_out, p_init,
+                                     r_init, p_final, r_final, static_cast<cudaStream_t>(stream));
+}
+
+const char *fd_last_error(void) { return fdsweep::last_error(); }
+
+const char *fd_version(void) { return "fdsweep 0.1 (sm_103a)"; }
+
+fd_status fd_stats_enable(int on) { return fdsweep::stats_enable(on); }
+fd_status fd_stats_reset(void) { return fdsweep::stats_reset(); }
+fd_status fd_stats_get(const char *family, double *total_ms, int64_t *launches,
+                       double *points_per_launch) {
+    return fdsweep::stats_get(family, total_ms, launches, points_per_launch);
+}
+
+fd_status fd_set_acoustic_config(int so, int config) {
+    if (!fdsweep::valid_so(so)) return fdsweep::set_error(FD_ERR_SO, "bad space order %d", so);
+    const int R = so / 2;
+    if (config < -1 || config >= fdsweep::acoustic_num_configs(R))
+        return fdsweep::set_error(FD_ERR_ARG, "config %d out of range for so %d", config, so);
+    fdsweep::g_acoustic_config[R] = config;
+    return FD_OK;
+}
+
+int fd_num_acoustic_configs(int so) {
+    return fdsweep::valid_so(so) ? fdsweep::acoustic_num_configs(so / 2) : 0;
+}
+
+}  // extern "C"

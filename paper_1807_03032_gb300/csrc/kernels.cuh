@@ -1,0 +1,135 @@
+// kernels.cuh -- argument blocks and host launchers of the fdsweep kernels.
+//
+// Device data layout (all FP32):
+//   wavefields  [nbuf][nz][ny][nxp], nxp = nx rounded up to a multiple of 4
+//               (16-byte rows for TMA and float4 access); buffer index
+//               (shot * fields_per_shot + level).  Columns nx..nxp-1 are
+//               padding that no kernel reads.
+//   coefficient fields (b = dt^2/(m + damp dt/2), TTI a, s, n) share the
+//               [nz][ny][nxp] layout.
+//   sparse tables one SparsePoint (16 bytes) per source/receiver.
+#pragma once
+
+#include "common.cuh"
+
+namespace fdsweep {
+
+struct WaveLayout {
+    int nx, ny, nz, nxp;
+    int64_t plane;  // ny * nxp
+    int64_t vol;    // nz * plane
+};
+
+// Trilinear stencil of one sparse point: index of the (x1, y1, z1) corner in
+// the padded layout and the fractional offsets along each axis (computed in
+// FP64, stored rounded to FP32).
+struct SparsePoint {
+    uint32_t base;
+    float fx, fy, fz;
+};
+
+constexpr int kMaxRadius = 8;
+
+// ---------------------------------------------------------------- acoustic K1
+
+struct AcousticStepArgs {
+    float *wave;          // 2 buffers per shot: index 2 s + level
+    const float *bcoef;   // b = dt^2 / (m + damp dt / 2)
+    const float *dpx;     // damp_x / dt, [nx]
+    const float *dpy;     // damp_y / dt, [ny]
+    const float *dpz;     // damp_z / dt, [nz]
+    WaveLayout L;
+    int nshots;
+    int cur;              // level holding u^n (u^{n-1} and u^{n+1} share the other)
+    float wc;             // sum over axes of w_0 / h_d^2
+    float wx[kMaxRadius + 1], wy[kMaxRadius + 1], wz[kMaxRadius + 1];  // w_k / h_d^2
+    unsigned int *err;
+};
+
+struct AcousticPlan {
+    int radius = 0;
+    int config = 0;
+    CUtensorMap map;      // 4-D map over all wavefield buffers
+    dim3 grid, block;
+    size_t smem = 0;
+    int zchunk = 0, nzc = 1;
+    const char *name = "";
+};
+
+int acoustic_num_configs(int radius);
+int acoustic_default_config(int radius);
+fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots, float *wave,
+                        AcousticPlan *plan);
+fd_status acoustic_launch(const AcousticPlan &plan, const AcousticStepArgs &args,
+                          cudaStream_t stream);
+
+// ---------------------------------------------------------------- sparse K3/K4
+
+struct SparseArgs {
+    float *wave;                 // wavefield buffers
+    int fields_per_shot;         // 2 (acoustic) or 4 (TTI: p levels 0,1; r levels 2,3)
+    WaveLayout L;
+    const float *bcoef;          // injection scale per node
+    int nshots, nt;
+    // injection into level `inj_level[0]` (and `inj_level[1]` if >= 0)
+    int nsrc;
+    const SparsePoint *src_tab;  // [nshots][nsrc]
+    const float *src_wav;        // [nshots][nt][nsrc]
+    int inj_level0, inj_level1;
+    // interpolation of level `rec_level`
+    int nrec;
+    const SparsePoint *rec_tab;  // [nshots][nrec]
+    float *rec_out;              // [nshots][nt][nrec]
+    int rec_level;
+    const int *step_base;        // device counter added to `step` (may be null)
+};
+
+// One launch performs the injection of src[n] (if do_inject) and the
+// interpolation rec[n] (if do_interp), n = step + (*step_base if given).
+fd_status sparse_launch(const SparseArgs &a, int step, bool do_inject, bool do_interp,
+                        cudaStream_t stream);
+fd_status bump_counter(int *counter, int by, cudaStream_t stream);
+
+// ---------------------------------------------------------------- setup K0
+
+struct MediumStats {
+    float m_min, m_max;
+    float eps_max;
+    unsigned int flags;  // DEV_ERR_* bits
+};
+
+// b = dt^2 / (m + damp dt/2) in the padded layout; damp per-axis profiles
+// scaled by 1/dt into dps[nx + ny + nz].  m and damp are dense device arrays.
+fd_status setup_acoustic_coeffs(const float *m, const float *damp, double dt,
+                                const WaveLayout &L, float *bcoef, float *dps,
+                                MediumStats *dev_stats, cudaStream_t stream);
+// TTI extra fields: a = 1 + 2 eps, s = sqrt(1 + 2 delta), n = (nx, ny, nz).
+fd_status setup_tti_coeffs(const float *eps, const float *delta, const float *theta,
+                           const float *phi, const WaveLayout &L, float *acoef, float *scoef,
+                           float *nvec /* 3 fields */, MediumStats *dev_stats,
+                           cudaStream_t stream);
+fd_status setup_sparse_table(const float *xyz, int npts, const fd_grid &g, const WaveLayout &L,
+                             SparsePoint *tab, unsigned int *flags, cudaStream_t stream);
+fd_status init_medium_stats(MediumStats *dev_stats, cudaStream_t stream);
+// Sets DEV_ERR_NONFINITE in *flags if any element of the field is not finite.
+fd_status check_finite(const float *field, const WaveLayout &L, int nfields,
+                       unsigned int *flags, cudaStream_t stream);
+
+// ---------------------------------------------------------------- TTI K2a/K2b
+
+struct TtiArgs {
+    float *wave;           // 4 buffers per shot: p levels (0,1), r levels (2,3)
+    float *tmp;            // 6 temporaries per shot [6][vol]
+    const float *bcoef, *acoef, *scoef, *nvec;
+    const float *dpx, *dpy, *dpz;
+    WaveLayout L;
+    int nshots;
+    int cur;
+    float cx[kMaxRadius + 1], cy[kMaxRadius + 1], cz[kMaxRadius + 1];  // c_k / h_d
+    unsigned int *err;
+};
+
+fd_status tti_launch(int radius, const TtiArgs &a, cudaStream_t stream, float *ms_pass1,
+                     float *ms_pass2, cudaEvent_t *ev /* 3 events or null */);
+
+}  // namespace fdsweep

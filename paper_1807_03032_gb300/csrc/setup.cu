@@ -1,0 +1,233 @@
+// setup.cu -- K0: per-call coefficient precompute and validation.
+//
+//  * b = dt^2 / (m + damp dt / 2) per point (FP64 arithmetic, rounded once),
+//    the factor that multiplies the Laplacian in the leapfrog update and the
+//    injected source (Listing finject's dt^2 q / m, generalised to the damped
+//    update); damping profiles scaled by 1/dt.
+//  * TTI: a = 1 + 2 eps, s = sqrt(1 + 2 delta) and the symmetry axis
+//    n = (sin theta cos phi, sin theta sin phi, cos theta), precomputed once
+//    because they do not change with time.
+//  * Sparse tables: the trilinear corner and fractional offsets of every
+//    source and receiver, x1 = floor((x - o)/h) in FP64, clamped to n - 2.
+//  * Reductions for validation: min/max of m (stability bound), max eps,
+//    flags for non-finite or non-physical values.
+#include "kernels.cuh"
+
+namespace fdsweep {
+namespace {
+
+// Order-preserving float <-> uint mapping for atomicMin/atomicMax on floats.
+__device__ __forceinline__ unsigned int float_key(float f) {
+    const unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(unsigned int k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+struct StatsKeys {
+    unsigned int m_min, m_max, eps_max, flags;
+};
+
+__global__ void init_stats_kernel(StatsKeys *s) {
+    s->m_min = float_key(__int_as_float(0x7f800000));  // +inf
+    s->m_max = float_key(0.f);
+    s->eps_max = float_key(-__int_as_float(0x7f800000));
+    s->flags = 0u;
+}
+
+__global__ void finish_stats_kernel(StatsKeys *s) {
+    MediumStats *out = reinterpret_cast<MediumStats *>(s);
+    const StatsKeys k = *s;
+    out->m_min = key_float(k.m_min);
+    out->m_max = key_float(k.m_max);
+    out->eps_max = key_float(k.eps_max);
+    out->flags = k.flags;
+}
+
+__device__ __forceinline__ float warp_min(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__global__ void acoustic_coeff_kernel(const float *__restrict__ m, const float *__restrict__ damp,
+                                      double dt, WaveLayout L, float *__restrict__ bcoef,
+                                      StatsKeys *stats) {
+    const int64_t n = (int64_t)L.nx * L.ny * L.nz;
+    float lmin = __int_as_float(0x7f800000), lmax = 0.f;
+    unsigned int bad = 0u;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(p % L.nx);
+        const int64_t r = p / L.nx;
+        const int j = (int)(r % L.ny);
+        const int k = (int)(r / L.ny);
+        const float mv = m[p];
+        double d = 0.0;
+        if (damp) d = (double)damp[i] + (double)damp[L.nx + j] + (double)damp[L.nx + L.ny + k];
+        if (!(mv > 0.f) || !isfinite(mv) || !(d >= 0.0) || !isfinite(d)) bad = DEV_ERR_MEDIUM;
+        lmin = fminf(lmin, mv);
+        lmax = fmaxf(lmax, mv);
+        const double b = dt * dt / ((double)mv + 0.5 * d * dt);
+        bcoef[(int64_t)k * L.plane + (int64_t)j * L.nxp + i] = (float)b;
+    }
+    lmin = warp_min(lmin);
+    lmax = warp_max(lmax);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&stats->m_min, float_key(lmin));
+        atomicMax(&stats->m_max, float_key(lmax));
+    }
+    if (bad) atomicOr(&stats->flags, bad);
+}
+
+__global__ void damp_scale_kernel(const float *__restrict__ damp, int n, double dt,
+                                  float *__restrict__ dps) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dps[i] = damp ? (float)((double)damp[i] / dt) : 0.f;
+}
+
+__global__ void tti_coeff_kernel(const float *__restrict__ eps, const float *__restrict__ delta,
+                                 const float *__restrict__ theta, const float *__restrict__ phi,
+                                 WaveLayout L, float *__restrict__ acoef, float *__restrict__ scoef,
+                                 float *__restrict__ nvec, StatsKeys *stats) {
+    const int64_t n = (int64_t)L.nx * L.ny * L.nz;
+    float lmax = -__int_as_float(0x7f800000);
+    unsigned int bad = 0u;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(p % L.nx);
+        const int64_t r = p / L.nx;
+        const int j = (int)(r % L.ny);
+        const int k = (int)(r / L.ny);
+        const float e = eps[p], d = delta[p], th = theta[p], ph = phi[p];
+        if (!isfinite(e) || !isfinite(d) || !isfinite(th) || !isfinite(ph) || !(e >= d) ||
+            !(1.0f + 2.0f * d >= 0.f))
+            bad = DEV_ERR_MEDIUM;
+        lmax = fmaxf(lmax, e);
+        const int64_t q = (int64_t)k * L.plane + (int64_t)j * L.nxp + i;
+        acoef[q] = (float)(1.0 + 2.0 * (double)e);
+        scoef[q] = (float)sqrt(fmax(0.0, 1.0 + 2.0 * (double)d));
+        double st, ct, sp, cp;
+        sincos((double)th, &st, &ct);
+        sincos((double)ph, &sp, &cp);
+        nvec[q] = (float)(st * cp);
+        nvec[L.vol + q] = (float)(st * sp);
+        nvec[2 * L.vol + q] = (float)ct;
+    }
+    lmax = warp_max(lmax);
+    if ((threadIdx.x & 31) == 0) atomicMax(&stats->eps_max, float_key(lmax));
+    if (bad) atomicOr(&stats->flags, bad);
+}
+
+__global__ void sparse_table_kernel(const float *__restrict__ xyz, int npts, fd_grid g,
+                                    WaveLayout L, SparsePoint *__restrict__ tab,
+                                    unsigned int *flags) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npts) return;
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const double h[3] = {g.hx, g.hy, g.hz};
+    const double o[3] = {g.ox, g.oy, g.oz};
+    int i1[3];
+    float fr[3];
+    bool ok = true;
+    for (int a = 0; a < 3; ++a) {
+        const double s = ((double)xyz[3 * (int64_t)p + a] - o[a]) / h[a];
+        if (!(s >= 0.0 && s <= (double)(n[a] - 1))) {
+            ok = false;
+            i1[a] = 0;
+            fr[a] = 0.f;
+            continue;
+        }
+        int x1 = (int)floor(s);
+        if (x1 > n[a] - 2) x1 = n[a] - 2;
+        i1[a] = x1;
+        fr[a] = (float)(s - (double)x1);
+    }
+    if (!ok) atomicOr(flags, DEV_ERR_COORD);
+    SparsePoint sp;
+    sp.base = (uint32_t)((int64_t)i1[2] * L.plane + (int64_t)i1[1] * L.nxp + i1[0]);
+    sp.fx = fr[0];
+    sp.fy = fr[1];
+    sp.fz = fr[2];
+    tab[p] = sp;
+}
+
+__global__ void finite_kernel(const float *__restrict__ f, int64_t n, unsigned int *flags) {
+    bool bad = false;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(f[p])) bad = true;
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, DEV_ERR_NONFINITE);
+}
+
+int grid_for(int64_t n, int threads) {
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int64_t b = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)nsm * 8;
+    if (b > cap) b = cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+fd_status init_medium_stats(MediumStats *dev_stats, cudaStream_t stream) {
+    static_assert(sizeof(StatsKeys) == sizeof(MediumStats), "stats layout");
+    init_stats_kernel<<<1, 1, 0, stream>>>(reinterpret_cast<StatsKeys *>(dev_stats));
+    FD_CUDA_TRY(cudaGetLastError());
+    return FD_OK;
+}
+
+fd_status setup_acoustic_coeffs(const float *m, const float *damp, double dt,
+                                const WaveLayout &L, float *bcoef, float *dps,
+                                MediumStats *dev_stats, cudaStream_t stream) {
+    StatsKeys *keys = reinterpret_cast<StatsKeys *>(dev_stats);
+    const int64_t n = (int64_t)L.nx * L.ny * L.nz;
+    acoustic_coeff_kernel<<<grid_for(n, 256), 256, 0, stream>>>(m, damp, dt, L, bcoef, keys);
+    FD_CUDA_TRY(cudaGetLastError());
+    const int nd = L.nx + L.ny + L.nz;
+    damp_scale_kernel<<<(nd + 255) / 256, 256, 0, stream>>>(damp, nd, dt, dps);
+    FD_CUDA_TRY(cudaGetLastError());
+    return FD_OK;
+}
+
+fd_status setup_tti_coeffs(const float *eps, const float *delta, const float *theta,
+                           const float *phi, const WaveLayout &L, float *acoef, float *scoef,
+                           float *nvec, MediumStats *dev_stats, cudaStream_t stream) {
+    StatsKeys *keys = reinterpret_cast<StatsKeys *>(dev_stats);
+    const int64_t n = (int64_t)L.nx * L.ny * L.nz;
+    tti_coeff_kernel<<<grid_for(n, 256), 256, 0, stream>>>(eps, delta, theta, phi, L, acoef,
+                                                           scoef, nvec, keys);
+    FD_CUDA_TRY(cudaGetLastError());
+    return FD_OK;
+}
+
+fd_status setup_sparse_table(const float *xyz, int npts, const fd_grid &g, const WaveLayout &L,
+                             SparsePoint *tab, unsigned int *flags, cudaStream_t stream) {
+    if (npts <= 0) return FD_OK;
+    sparse_table_kernel<<<(npts + 255) / 256, 256, 0, stream>>>(xyz, npts, g, L, tab, flags);
+    FD_CUDA_TRY(cudaGetLastError());
+    return FD_OK;
+}
+
+fd_status check_finite(const float *field, const WaveLayout &L, int nfields, unsigned int *flags,
+                       cudaStream_t stream) {
+    const int64_t n = L.vol * nfields;
+    finite_kernel<<<grid_for(n, 256), 256, 0, stream>>>(field, n, flags);
+    FD_CUDA_TRY(cudaGetLastError());
+    return FD_OK;
+}
+
+// Converts the reduction keys into MediumStats in place (device side).
+fd_status finish_medium_stats(MediumStats *dev_stats, cudaStream_t stream) {
+    finish_stats_kernel<<<1, 1, 0, stream>>>(reinterpret_cast<StatsKeys *>(dev_stats));
+    FD_CUDA_TRY(cudaGetLastError());
+    return FD_OK;
+}
+
+}  // namespace fdsweep

@@ -1,0 +1,84 @@
+// sparse.cu -- K3/K4: sparse source injection and receiver interpolation.
+//
+// Trilinear interpolation (Eq. interp, the tensor product of the 1-D linear
+// weights 1 - frac and frac along x, y and z) gathers
+//   rec[n][i] = sum_c w_c u^n(node_c),
+// and injection, its adjoint (Listing finject), scatters
+//   u^{n+1}(node_c) += w_c * b(node_c) * q[n],  b = dt^2 / (m + damp dt/2),
+// with atomicAdd so that sources sharing a node accumulate (injection is a
+// reduction).  One launch does both: receiver threads first, then one thread
+// per (source, corner).
+#include "kernels.cuh"
+
+namespace fdsweep {
+namespace {
+
+__device__ __forceinline__ float corner_weight(const SparsePoint &p, int c) {
+    const float wx = (c & 1) ? p.fx : 1.f - p.fx;
+    const float wy = (c & 2) ? p.fy : 1.f - p.fy;
+    const float wz = (c & 4) ? p.fz : 1.f - p.fz;
+    return wx * wy * wz;
+}
+
+__device__ __forceinline__ int64_t corner_offset(const SparsePoint &p, int c, const WaveLayout &L) {
+    return (int64_t)p.base + ((c & 1) ? 1 : 0) + ((c & 2) ? L.nxp : 0) + ((c & 4) ? L.plane : 0);
+}
+
+// Threads [0, nrec_total) interpolate receivers (nrec_total = 0 when only
+// injecting); the following nshots*nsrc*8 threads inject.
+__global__ void sparse_kernel(const SparseArgs a, int step, int do_inject, int64_t nrec_total) {
+    const int n = step + (a.step_base ? *a.step_base : 0);
+    if (n < 0 || n >= a.nt) return;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid < nrec_total) {
+        const int s = (int)(gid / a.nrec);
+        const int i = (int)(gid - (int64_t)s * a.nrec);
+        const SparsePoint p = a.rec_tab[gid];
+        const float *u = a.wave + (int64_t)(s * a.fields_per_shot + a.rec_level) * a.L.vol;
+        float acc = 0.f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc = fmaf(corner_weight(p, c), __ldg(u + corner_offset(p, c, a.L)), acc);
+        a.rec_out[((int64_t)s * a.nt + n) * a.nrec + i] = acc;
+        return;
+    }
+    if (!do_inject) return;
+    const int64_t k = gid - nrec_total;
+    if (k >= (int64_t)a.nshots * a.nsrc * 8) return;
+    const int c = (int)(k & 7);
+    const int64_t ps = k >> 3;  // (shot, source)
+    const int s = (int)(ps / a.nsrc);
+    const int isrc = (int)(ps - (int64_t)s * a.nsrc);
+    const SparsePoint p = a.src_tab[ps];
+    const int64_t off = corner_offset(p, c, a.L);
+    const float q = a.src_wav[((int64_t)s * a.nt + n) * a.nsrc + isrc];
+    const float val = corner_weight(p, c) * __ldg(a.bcoef + off) * q;
+    atomicAdd(a.wave + (int64_t)(s * a.fields_per_shot + a.inj_level0) * a.L.vol + off, val);
+    if (a.inj_level1 >= 0)
+        atomicAdd(a.wave + (int64_t)(s * a.fields_per_shot + a.inj_level1) * a.L.vol + off, val);
+}
+
+__global__ void bump_kernel(int *counter, int by) { *counter += by; }
+
+}  // namespace
+
+fd_status sparse_launch(const SparseArgs &a, int step, bool do_inject, bool do_interp,
+                        cudaStream_t stream) {
+    const int64_t nrec_total = do_interp ? (int64_t)a.nshots * a.nrec : 0;
+    const int64_t ninj = do_inject ? (int64_t)a.nshots * a.nsrc * 8 : 0;
+    const int64_t total = nrec_total + ninj;
+    if (total == 0) return FD_OK;
+    const int threads = 256;
+    const int64_t blocks = (total + threads - 1) / threads;
+    sparse_kernel<<<(unsigned)blocks, threads, 0, stream>>>(a, step, do_inject ? 1 : 0,
+                                                            nrec_total);
+    FD_CUDA_TRY(cudaGetLastError());
+    return FD_OK;
+}
+
+fd_status bump_counter(int *counter, int by, cudaStream_t stream) {
+    bump_kernel<<<1, 1, 0, stream>>>(counter, by);
+    FD_CUDA_TRY(cudaGetLastError());
+    return FD_OK;
+}
+
+}  // namespace fdsweep

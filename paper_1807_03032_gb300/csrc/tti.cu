@@ -1,0 +1,129 @@
+// tti.cu -- K2a/K2b: one leapfrog step of the pseudo-acoustic TTI system.
+//
+// The rotated operators are built from central first derivatives D_i of
+// radius R (section "Test case setup": two coupled acoustic equations whose
+// Laplacians come from spatially rotated first-derivative operators):
+//   Hz q = sum_i D_i(n_i (n . grad q)),   Hxy q = sum_i D_i D_i q - Hz q.
+// Since D is linear, Hxy p = sum_i D_i f_i with f_i = D_i p - n_i (n . grad p)
+// and Hz r = sum_i D_i e_i with e_i = n_i (n . grad r).  Only Hxy p and Hz r
+// enter the update
+//   m p_tt + damp p_t = a Hxy p + s Hz r,   m r_tt + damp r_t = s Hxy p + Hz r,
+// (a = 1 + 2 eps, s = sqrt(1 + 2 delta)), so pass 1 (K2a) writes the six
+// first-derivative temporaries f (of p) and e (of r), computed once per point
+// and reused by every stencil point of pass 2 -- the shift-invariant reuse the
+// paper's SIE pass performs -- and pass 2 (K2b) applies the second
+// first-derivative and the centred damped leapfrog
+//   q+ = q + (1 - zeta)(q - q-) + b * rhs_q,  b = dt^2/(m + damp dt/2),
+//   zeta = damp * b / dt.
+// Temporaries outside the grid are zero ghosts, like the fields.
+#include "kernels.cuh"
+
+namespace fdsweep {
+namespace {
+
+constexpr int TBX = 32, TBY = 8;
+
+template <int R>
+__device__ __forceinline__ float dfirst(const float *__restrict__ f, int64_t q, int64_t stride,
+                                        int idx, int n, const float *c) {
+    // sum_k c_k (f[idx+k] - f[idx-k]) with zero ghosts outside [0, n)
+    float d = 0.f;
+#pragma unroll
+    for (int k = 1; k <= R; ++k) {
+        const float fp = (idx + k < n) ? __ldg(f + q + k * stride) : 0.f;
+        const float fm = (idx - k >= 0) ? __ldg(f + q - k * stride) : 0.f;
+        d = fmaf(c[k], fp - fm, d);
+    }
+    return d;
+}
+
+template <int R>
+__global__ void __launch_bounds__(TBX *TBY) tti_pass1_kernel(const TtiArgs a) {
+    const int i = blockIdx.x * TBX + threadIdx.x;
+    const int j = blockIdx.y * TBY + threadIdx.y;
+    const int k = blockIdx.z % a.L.nz;
+    const int s = blockIdx.z / a.L.nz;
+    if (i >= a.L.nx || j >= a.L.ny) return;
+    const WaveLayout &L = a.L;
+    const int64_t q = (int64_t)k * L.plane + (int64_t)j * L.nxp + i;
+    const float *p = a.wave + (int64_t)(4 * s + a.cur) * L.vol;
+    const float *r = a.wave + (int64_t)(4 * s + 2 + a.cur) * L.vol;
+    const float gpx = dfirst<R>(p, q, 1, i, L.nx, a.cx);
+    const float gpy = dfirst<R>(p, q, L.nxp, j, L.ny, a.cy);
+    const float gpz = dfirst<R>(p, q, L.plane, k, L.nz, a.cz);
+    const float grx = dfirst<R>(r, q, 1, i, L.nx, a.cx);
+    const float gry = dfirst<R>(r, q, L.nxp, j, L.ny, a.cy);
+    const float grz = dfirst<R>(r, q, L.plane, k, L.nz, a.cz);
+    const float nx = __ldg(a.nvec + q), ny = __ldg(a.nvec + L.vol + q),
+                nz = __ldg(a.nvec + 2 * L.vol + q);
+    const float hp = nx * gpx + ny * gpy + nz * gpz;
+    const float hr = nx * grx + ny * gry + nz * grz;
+    float *t = a.tmp + (int64_t)6 * s * L.vol;
+    t[q] = gpx - nx * hp;
+    t[L.vol + q] = gpy - ny * hp;
+    t[2 * L.vol + q] = gpz - nz * hp;
+    t[3 * L.vol + q] = nx * hr;
+    t[4 * L.vol + q] = ny * hr;
+    t[5 * L.vol + q] = nz * hr;
+}
+
+template <int R>
+__global__ void __launch_bounds__(TBX *TBY) tti_pass2_kernel(const TtiArgs a) {
+    const int i = blockIdx.x * TBX + threadIdx.x;
+    const int j = blockIdx.y * TBY + threadIdx.y;
+    const int k = blockIdx.z % a.L.nz;
+    const int s = blockIdx.z / a.L.nz;
+    if (i >= a.L.nx || j >= a.L.ny) return;
+    const WaveLayout &L = a.L;
+    const int64_t q = (int64_t)k * L.plane + (int64_t)j * L.nxp + i;
+    const float *t = a.tmp + (int64_t)6 * s * L.vol;
+    const float A = dfirst<R>(t, q, 1, i, L.nx, a.cx) +
+                    dfirst<R>(t + L.vol, q, L.nxp, j, L.ny, a.cy) +
+                    dfirst<R>(t + 2 * L.vol, q, L.plane, k, L.nz, a.cz);
+    const float B = dfirst<R>(t + 3 * L.vol, q, 1, i, L.nx, a.cx) +
+                    dfirst<R>(t + 4 * L.vol, q, L.nxp, j, L.ny, a.cy) +
+                    dfirst<R>(t + 5 * L.vol, q, L.plane, k, L.nz, a.cz);
+    float *p = a.wave + (int64_t)(4 * s + a.cur) * L.vol;
+    float *pn = a.wave + (int64_t)(4 * s + 1 - a.cur) * L.vol;
+    float *r = a.wave + (int64_t)(4 * s + 2 + a.cur) * L.vol;
+    float *rn = a.wave + (int64_t)(4 * s + 3 - a.cur) * L.vol;
+    const float b = __ldg(a.bcoef + q), av = __ldg(a.acoef + q), sv = __ldg(a.scoef + q);
+    const float zeta = (a.dpx[i] + a.dpy[j] + a.dpz[k]) * b;
+    const float pc = p[q], pm = pn[q], rc = r[q], rm = rn[q];
+    pn[q] = pc + (1.f - zeta) * (pc - pm) + b * (av * A + sv * B);
+    rn[q] = rc + (1.f - zeta) * (rc - rm) + b * (sv * A + B);
+}
+
+template <int R>
+fd_status launch_r(const TtiArgs &a, cudaStream_t stream, cudaEvent_t *ev) {
+    dim3 block(TBX, TBY, 1);
+    dim3 grid((a.L.nx + TBX - 1) / TBX, (a.L.ny + TBY - 1) / TBY, a.L.nz * a.nshots);
+    if (ev) FD_CUDA_TRY(cudaEventRecord(ev[0], stream));
+    tti_pass1_kernel<R><<<grid, block, 0, stream>>>(a);
+    FD_CUDA_TRY(cudaGetLastError());
+    if (ev) FD_CUDA_TRY(cudaEventRecord(ev[1], stream));
+    tti_pass2_kernel<R><<<grid, block, 0, stream>>>(a);
+    FD_CUDA_TRY(cudaGetLastError());
+    if (ev) FD_CUDA_TRY(cudaEventRecord(ev[2], stream));
+    return FD_OK;
+}
+
+}  // namespace
+
+fd_status tti_launch(int radius, const TtiArgs &a, cudaStream_t stream, float *ms_pass1,
+                     float *ms_pass2, cudaEvent_t *ev) {
+    (void)ms_pass1;
+    (void)ms_pass2;
+    if ((int64_t)a.L.nz * a.nshots > 65535)
+        return set_error(FD_ERR_ARG, "TTI launch: nz * nshots exceeds 65535");
+    switch (radius) {
+        case 1: return launch_r<1>(a, stream, ev);
+        case 2: return launch_r<2>(a, stream, ev);
+        case 4: return launch_r<4>(a, stream, ev);
+        case 6: return launch_r<6>(a, stream, ev);
+        case 8: return launch_r<8>(a, stream, ev);
+        default: return set_error(FD_ERR_SO, "no TTI kernel for radius %d", radius);
+    }
+}
+
+}  // namespace fdsweep

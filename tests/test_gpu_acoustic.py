@@ -1,0 +1,257 @@
+"""GPU parity of the acoustic forward path (K0 setup, K1 stencil, K3/K4 sparse,
+graph-captured time loop) against the FP64 oracle, through the C ABI."""
+import functools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from tests.gpu_util import TOL, rel_l2, require_cuda, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@functools.lru_cache(maxsize=None)
+def long_run_trace_norm(so):
+    w = workloads.acoustic_small(so=so, nt=400)
+    og = oracle.make_grid(w.shape, w.spacing, w.origin)
+    rref, _ = oracle.acoustic_forward(og, w.so, w.dt, w.nt, w.m, w.src_xyz, w.src_wav,
+                                      w.rec_xyz, damp=w.damp)
+    return float(np.linalg.norm(rref))
+
+
+def run_pair(w, damp=True, u_init=None, host=False):
+    torch = require_cuda()
+    import paper_1807_03032_gb300 as fd
+    g = fd.Grid(w.shape, w.spacing, w.origin)
+    d = w.damp if damp else None
+    if host:
+        rec, uf = fd.acoustic_forward(g, w.so, w.dt, w.nt, w.m, w.src_xyz, w.src_wav, w.rec_xyz,
+                                      damp=d, u_init=u_init)
+    else:
+        m, sx, sw, rx, dd, ui = to_dev(torch, w.m, w.src_xyz, w.src_wav, w.rec_xyz, d, u_init)
+        rec, uf = fd.acoustic_forward(g, w.so, w.dt, w.nt, m, sx, sw, rx, damp=dd, u_init=ui)
+        torch.cuda.synchronize()
+        rec, uf = rec.cpu().numpy(), uf.cpu().numpy()
+    og = oracle.make_grid(w.shape, w.spacing, w.origin)
+    rref, uref = oracle.acoustic_forward(og, w.so, w.dt, w.nt, w.m, w.src_xyz, w.src_wav,
+                                         w.rec_xyz, damp=d, u_init=u_init)
+    return rec, uf, rref, uref
+
+
+@pytest.mark.parametrize("so", [4, 8, 12, 16])
+def test_small_config_parity(so):
+    """64^3 two-layer model, 10-point border, so 4..16, nt = 100."""
+    w = workloads.acoustic_small(so=so, nt=100)
+    rec, uf, rref, uref = run_pair(w)
+    assert rel_l2(uf, uref) <= TOL
+    # By t = 150 ms only the wavelet's precursor has reached the receivers:
+    # compare the traces against a floor of 1e-3 times the trace norm of the
+    # nt = 400 run, in which the direct and reflected waves arrive.
+    floor = 1e-3 * long_run_trace_norm(so)
+    assert rel_l2(rec, rref, floor=floor) <= TOL
+    assert np.all(np.isfinite(uf))
+
+
+@pytest.mark.parametrize("so", [4, 16])
+def test_small_config_long_run_traces(so):
+    """nt = 400: the direct and reflected waves reach the receiver line."""
+    w = workloads.acoustic_small(so=so, nt=400)
+    rec, uf, rref, uref = run_pair(w)
+    assert np.linalg.norm(rref) > 1e-3
+    assert rel_l2(rec, rref) <= TOL
+    assert rel_l2(uf, uref) <= TOL
+
+
+def ragged_problem(so, nshots=2, nt=37, seed=3):
+    """Ragged box (nx not a multiple of 4, partial tiles in x and y, odd nz),
+    anisotropic spacing, shifted origin, several shots, colliding sources,
+    random initial state."""
+    shape = (31, 23, 45)  # nz, ny, nx
+    h = (9.0, 11.0, 10.0)
+    o = (-100.0, 250.0, 30.0)
+    rng = np.random.default_rng(seed)
+    v = 1.5 + 2.0 * workloads.smooth_random(shape, seed, 3.0, 0.0, 1.0)
+    m = workloads.slowness_squared(v)
+    damp = workloads.damping_profile(shape, 5, h, 3.5)
+    dt = 0.9 * workloads.cfl_dt(h, 3.5)
+    ext = np.array([(shape[2] - 1) * h[0], (shape[1] - 1) * h[1], (shape[0] - 1) * h[2]])
+    nsrc, nrec = 3, 17
+    src = o + rng.uniform(0.05, 0.95, (nshots, nsrc, 3)) * ext
+    src[:, 1] = src[:, 0]  # two sources on the same point
+    rec = o + rng.uniform(0.0, 1.0, (nshots, nrec, 3)) * ext
+    rec[:, 0] = o + ext       # last node in every axis
+    rec[:, 1] = o             # origin
+    wav = rng.standard_normal((nshots, nt, nsrc))
+    u_init = 1e-2 * workloads.random_wavefields(shape, seed, nshots=nshots, sigma=2.0)
+    return workloads.Workload("ragged", shape, h, o, so, dt, nt, m, damp,
+                              src.astype(np.float32), wav.astype(np.float32),
+                              rec.astype(np.float32)), u_init
+
+
+@pytest.mark.parametrize("so", [2, 4, 8, 12, 16])
+def test_ragged_multishot_parity(so):
+    w, u_init = ragged_problem(so)
+    rec, uf, rref, uref = run_pair(w, u_init=u_init)
+    assert rel_l2(uf, uref) <= TOL
+    assert rel_l2(rec, rref) <= TOL
+    for s in range(w.nshots):
+        assert rel_l2(uf[s], uref[s]) <= TOL
+
+
+def test_host_buffers_match_device_buffers():
+    w, u_init = ragged_problem(8, nshots=1, nt=20)
+    torch = require_cuda()
+    rec_h, uf_h, rref, uref = run_pair(w, u_init=u_init, host=True)
+    rec_d, uf_d, _, _ = run_pair(w, u_init=u_init, host=False)
+    np.testing.assert_array_equal(uf_h, uf_d)
+    np.testing.assert_array_equal(rec_h, rec_d)
+    assert rel_l2(uf_h, uref) <= TOL
+    del torch
+
+
+def test_no_steps_no_sparse_points():
+    """nt = 1 (no step): the final state is the initial state and the single
+    trace sample interpolates it; nsrc = nrec = 0 is accepted."""
+    torch = require_cuda()
+    import paper_1807_03032_gb300 as fd
+    w, u_init = ragged_problem(4, nshots=1, nt=1)
+    rec, uf, rref, uref = run_pair(w, u_init=u_init)
+    np.testing.assert_array_equal(uf, u_init)
+    assert rel_l2(rec, rref) <= 1e-6
+    g = fd.Grid(w.shape, w.spacing, w.origin)
+    m, = to_dev(torch, w.m)
+    empty = torch.zeros((1, 0, 3), device="cuda")
+    rec2, uf2 = fd.acoustic_forward(g, 4, w.dt, 5, m, empty, torch.zeros((1, 5, 0), device="cuda"),
+                                    empty)
+    assert rec2.shape == (1, 5, 0)
+    assert float(uf2.abs().max()) == 0.0
+
+
+def test_all_tile_configs_agree_bitwise_and_runs_are_deterministic():
+    """Every compiled tile shape evaluates each point with the same operation
+    order, so all configurations give bit-identical results; a repeated run
+    is bit-identical too (sources on distinct nodes)."""
+    require_cuda()
+    from paper_1807_03032_gb300 import _native
+    for so in (2, 4, 8, 12, 16):
+        w, u_init = ragged_problem(so, nshots=1, nt=12)
+        w.src_xyz[:, 1] += 7.0
+        outs = []
+        try:
+            for cfg in range(_native.num_acoustic_configs(so)):
+                _native.set_acoustic_config(so, cfg)
+                outs.append(_gpu_only(w, u_init))
+            again = _gpu_only(w, u_init)
+        finally:
+            _native.set_acoustic_config(so, -1)
+        for rec, uf in outs[1:] + [again]:
+            np.testing.assert_array_equal(uf, outs[0][1])
+            np.testing.assert_array_equal(rec, outs[0][0])
+
+
+def _gpu_only(w, u_init):
+    torch = require_cuda()
+    import paper_1807_03032_gb300 as fd
+    g = fd.Grid(w.shape, w.spacing, w.origin)
+    m, sx, sw, rx, dd, ui = to_dev(torch, w.m, w.src_xyz, w.src_wav, w.rec_xyz, w.damp, u_init)
+    rec, uf = fd.acoustic_forward(g, w.so, w.dt, w.nt, m, sx, sw, rx, damp=dd, u_init=ui)
+    torch.cuda.synchronize()
+    return rec.cpu().numpy(), uf.cpu().numpy()
+
+
+def test_graph_path_equals_direct_launches():
+    """Statistics mode launches every step directly; the default path replays
+    a captured graph.  Both must give identical results (nt > 2 chunks)."""
+    from paper_1807_03032_gb300 import _native
+    w, u_init = ragged_problem(8, nshots=1, nt=70)
+    a = _gpu_only(w, u_init)
+    _native.stats_enable(True)
+    try:
+        b = _gpu_only(w, u_init)
+    finally:
+        _native.stats_enable(False)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    ms, n, pts = _native.stats_get("acoustic_step")
+    assert n >= 69 and ms > 0 and pts == float(np.prod(w.shape))
+
+
+def test_errors_are_reported():
+    torch = require_cuda()
+    import paper_1807_03032_gb300 as fd
+    from paper_1807_03032_gb300 import FdError
+    w = workloads.acoustic_small(so=4, nt=10)
+    g = fd.Grid(w.shape, w.spacing, w.origin)
+    m, sx, sw, rx = to_dev(torch, w.m, w.src_xyz, w.src_wav, w.rec_xyz)
+    # dt above the stability bound (bound = 0.5 h / v_max for so = 4)
+    with pytest.raises(FdError) as e:
+        fd.acoustic_forward(g, 4, 0.51 * 10.0 / 2.5, 10, m, sx, sw, rx)
+    assert e.value.name == "FD_ERR_CFL"
+    fd.acoustic_forward(g, 4, 0.49 * 10.0 / 2.5, 10, m, sx, sw, rx)
+    with pytest.raises(FdError) as e:
+        fd.acoustic_forward(g, 6, w.dt, 10, m, sx, sw, rx)
+    assert e.value.name == "FD_ERR_SO"
+    bad = rx.clone()
+    bad[0, 3, 2] = 64 * 10.0  # one cell beyond the last node
+    with pytest.raises(FdError) as e:
+        fd.acoustic_forward(g, 4, w.dt, 10, m, sx, sw, bad)
+    assert e.value.name == "FD_ERR_COORD"
+    m2 = m.clone()
+    m2[3, 4, 5] = -1.0
+    with pytest.raises(FdError) as e:
+        fd.acoustic_forward(g, 4, w.dt, 10, m2, sx, sw, rx)
+    assert e.value.name == "FD_ERR_ARG"
+    m2[3, 4, 5] = float("nan")
+    with pytest.raises(FdError) as e:
+        fd.acoustic_forward(g, 4, w.dt, 10, m2, sx, sw, rx)
+    assert e.value.name == "FD_ERR_ARG"
+    # the library still works after the errors
+    rec, _ = fd.acoustic_forward(g, 4, w.dt, 10, m, sx, sw, rx)
+    assert torch.isfinite(rec).all()
+
+
+def test_full_size_parity_first_steps():
+    """512^3 (the benchmark's grid and launch configuration), so = 8 and 16:
+    four steps from a smooth random state with a source and the full
+    512 x 512 receiver plane, against the oracle at every point."""
+    torch = require_cuda()
+    import paper_1807_03032_gb300 as fd
+    n = 512
+    for so in (8, 16):
+        w = workloads.acoustic_large(n=n, so=so, nt=4)
+        u_init = 0.01 * workloads.random_wavefields(w.shape, 21, sigma=6.0)
+        g = fd.Grid(w.shape, w.spacing, w.origin)
+        m, sx, sw, rx, dd, ui = to_dev(torch, w.m, w.src_xyz, w.src_wav, w.rec_xyz, w.damp,
+                                       u_init)
+        rec, uf = fd.acoustic_forward(g, so, w.dt, w.nt, m, sx, sw, rx, damp=dd, u_init=ui)
+        torch.cuda.synchronize()
+        rec, uf = rec.cpu().numpy(), uf.cpu().numpy()
+        del m, sx, sw, rx, dd, ui
+        og = oracle.make_grid(w.shape, w.spacing, w.origin)
+        rref, uref = oracle.acoustic_forward(og, so, w.dt, w.nt, w.m, w.src_xyz, w.src_wav,
+                                             w.rec_xyz, damp=w.damp, u_init=u_init)
+        assert rel_l2(uf, uref) <= TOL
+        assert rel_l2(rec, rref) <= TOL
+        del uf, uref
+
+
+def test_full_size_full_run_is_linear_in_the_source():
+    """512^3, so = 8, the full 1000 ms (594 steps): doubling the wavelet doubles
+    every trace sample exactly (FP32 scaling by 2 is exact), and the field
+    stays finite."""
+    torch = require_cuda()
+    import paper_1807_03032_gb300 as fd
+    w = workloads.acoustic_large(n=512, so=8)
+    g = fd.Grid(w.shape, w.spacing, w.origin)
+    m, sx, sw, rx, dd = to_dev(torch, w.m, w.src_xyz, w.src_wav, w.rec_xyz, w.damp)
+    rec1, uf1 = fd.acoustic_forward(g, 8, w.dt, w.nt, m, sx, sw, rx, damp=dd, return_final=False)
+    rec2, _ = fd.acoustic_forward(g, 8, w.dt, w.nt, m, sx, 2 * sw, rx, damp=dd,
+                                  return_final=False)
+    torch.cuda.synchronize()
+    assert torch.isfinite(rec1).all()
+    assert float(rec1.abs().max()) > 0
+    assert torch.equal(rec2, 2 * rec1)
+    assert w.nt == 594 and math.isclose(w.dt, 0.38 * 20.0 / 4.5)

@@ -1,0 +1,105 @@
+"""GPU parity of the TTI forward path (K2a/K2b + sparse) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from tests.gpu_util import TOL, rel_l2, require_cuda, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def run_pair(w, p_init=None, r_init=None):
+    torch = require_cuda()
+    import paper_1807_03032_gb300 as fd
+    g = fd.Grid(w.shape, w.spacing, w.origin)
+    dev = to_dev(torch, w.m, w.eps, w.delta, w.theta, w.phi, w.src_xyz, w.src_wav, w.rec_xyz,
+                 w.damp, p_init, r_init)
+    m, e, d, th, ph, sx, sw, rx, dd, pi, ri = dev
+    rec, pf, rf = fd.tti_forward(g, w.so, w.dt, w.nt, m, e, d, th, ph, sx, sw, rx, damp=dd,
+                                 p_init=pi, r_init=ri)
+    torch.cuda.synchronize()
+    og = oracle.make_grid(w.shape, w.spacing, w.origin)
+    rref, pref, qref = oracle.tti_forward(og, w.so, w.dt, w.nt, w.m, w.eps, w.delta, w.theta,
+                                          w.phi, w.src_xyz, w.src_wav, w.rec_xyz, damp=w.damp,
+                                          p_init=p_init, r_init=r_init)
+    return (rec.cpu().numpy(), pf.cpu().numpy(), rf.cpu().numpy()), (rref, pref, qref)
+
+
+@pytest.mark.parametrize("so", [4, 8, 12, 16])
+def test_small_tti_parity(so):
+    w = workloads.tti_small(so=so, nt=80)
+    (rec, pf, rf), (rref, pref, qref) = run_pair(w)
+    assert np.linalg.norm(rref) > 0
+    assert rel_l2(pf, pref) <= TOL
+    assert rel_l2(rf, qref) <= TOL
+    assert rel_l2(rec, rref) <= TOL
+
+
+@pytest.mark.parametrize("so", [2, 8, 16])
+def test_ragged_tti_multishot_parity(so):
+    """Ragged box, anisotropic spacing, two shots, random initial p and r,
+    theta and phi over their full range (n_z of either sign)."""
+    shape = (27, 21, 35)
+    h = (10.0, 12.0, 9.0)
+    o = (5.0, -40.0, 100.0)
+    rng = np.random.default_rng(5)
+    eps = rng.uniform(0.0, 0.3, shape)
+    delta = np.minimum(rng.uniform(-0.1, 0.2, shape), eps)
+    theta = rng.uniform(0.0, np.pi, shape)
+    phi = rng.uniform(-np.pi, np.pi, shape)
+    v = workloads.two_layer_velocity(shape, 1.8, 3.0)
+    dt = 0.9 * workloads.cfl_dt(h, 3.0, eps_max=0.3)
+    nt, nshots = 30, 2
+    ext = np.array([(shape[2] - 1) * h[0], (shape[1] - 1) * h[1], (shape[0] - 1) * h[2]])
+    src = o + rng.uniform(0.1, 0.9, (nshots, 2, 3)) * ext
+    rec = o + rng.uniform(0.0, 1.0, (nshots, 11, 3)) * ext
+    wav = rng.standard_normal((nshots, nt, 2))
+    f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    w = workloads.Workload("tti-ragged", shape, h, o, so, dt, nt, workloads.slowness_squared(v),
+                           workloads.damping_profile(shape, 4, h, 3.0), f32(src), f32(wav),
+                           f32(rec), eps=f32(eps), delta=f32(delta), theta=f32(theta),
+                           phi=f32(phi))
+    p_init = 1e-2 * workloads.random_wavefields(shape, 11, nshots=nshots, sigma=2.0)
+    r_init = 1e-2 * workloads.random_wavefields(shape, 12, nshots=nshots, sigma=2.0)
+    (rec, pf, rf), (rref, pref, qref) = run_pair(w, p_init, r_init)
+    assert rel_l2(pf, pref) <= TOL
+    assert rel_l2(rf, qref) <= TOL
+    assert rel_l2(rec, rref) <= TOL
+
+
+def test_tti_rejects_delta_above_eps_and_large_dt():
+    torch = require_cuda()
+    import paper_1807_03032_gb300 as fd
+    from paper_1807_03032_gb300 import FdError
+    w = workloads.tti_small(so=4, nt=5, n=24, nbl=4)
+    g = fd.Grid(w.shape, w.spacing, w.origin)
+    dev = to_dev(torch, w.m, w.eps, w.delta, w.theta, w.phi, w.src_xyz, w.src_wav, w.rec_xyz)
+    m, e, d, th, ph, sx, sw, rx = dev
+    d2 = d.clone()
+    d2[5, 5, 5] = e[5, 5, 5] + 0.05
+    with pytest.raises(FdError) as ex:
+        fd.tti_forward(g, 4, w.dt, w.nt, m, e, d2, th, ph, sx, sw, rx)
+    assert ex.value.name == "FD_ERR_ARG"
+    with pytest.raises(FdError) as ex:
+        fd.tti_forward(g, 4, 3.0 * w.dt, w.nt, m, e, d, th, ph, sx, sw, rx)
+    assert ex.value.name == "FD_ERR_CFL"
+    rec, _, _ = fd.tti_forward(g, 4, w.dt, w.nt, m, e, d, th, ph, sx, sw, rx)
+    assert torch.isfinite(rec).all()
+
+
+def test_tti_isotropic_limit_matches_between_fields():
+    """eps = delta = 0 and equal initial states: p and r stay equal (both are
+    advanced by the same sum Hxy p + Hz r when a = s = 1)."""
+    torch = require_cuda()
+    import paper_1807_03032_gb300 as fd
+    w = workloads.tti_small(so=8, nt=25, n=32, nbl=4)
+    z = np.zeros_like(w.eps)
+    g = fd.Grid(w.shape, w.spacing, w.origin)
+    dev = to_dev(torch, w.m, z, z, w.theta, w.phi, w.src_xyz, w.src_wav, w.rec_xyz, w.damp)
+    m, e, d, th, ph, sx, sw, rx, dd = dev
+    rec, pf, rf = fd.tti_forward(g, 8, w.dt, w.nt, m, e, d, th, ph, sx, sw, rx, damp=dd)
+    torch.cuda.synchronize()
+    scale = float(pf.abs().max())
+    assert scale > 0
+    assert float((pf - rf).abs().max()) <= 1e-5 * scale

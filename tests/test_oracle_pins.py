@@ -605,3 +605,24 @@ def _tti_energy_run(eps, delta, nt=150):
 def test_tti_bounded_when_eps_ge_delta_and_grows_otherwise():
     assert _tti_energy_run(0.3, 0.1) < 20.0
     assert _tti_energy_run(0.0, 0.6) > 1e3
+
+
+def test_reciprocity_inside_damping_layer():
+    """With the damped update (m+eta) u+ = dt^2 L u + 2 m u - (m-eta) u- + dt^2 P^T q
+    the z-transformed operator is symmetric, so reciprocity also holds for a
+    source and a receiver inside the absorbing border (different damping at
+    each); any other injection scale there breaks it."""
+    shape = (20, 20, 20)
+    h = (10.0, 10.0, 10.0)
+    g = grid(shape, h)
+    m = np.full(shape, np.float32(1 / 2.0 ** 2), dtype=np.float32)
+    dt = 0.38 * 10.0 / 2.0
+    nt = 40
+    damp = workloads.damping_profile(shape, 6, h, 2.0)
+    A = np.array([[[22.3, 81.7, 95.1]]], np.float32)   # x inside the border
+    B = np.array([[[121.9, 104.4, 11.2]]], np.float32)  # z inside the border
+    wav = workloads.ricker(nt, dt, f0=0.03)[None, :, None].astype(np.float32)
+    rAB, _ = oracle.acoustic_forward(g, 4, dt, nt, m, A, wav, B, damp=damp)
+    rBA, _ = oracle.acoustic_forward(g, 4, dt, nt, m, B, wav, A, damp=damp)
+    np.testing.assert_allclose(rAB, rBA, rtol=1e-10, atol=1e-12 * np.max(np.abs(rAB)))
+    assert np.max(np.abs(rAB)) > 0
