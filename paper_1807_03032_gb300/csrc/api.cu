@@ -110,16 +110,12 @@ struct Staged {
         user = p;
         count = n;
         host = p && n && !is_device_pointer(p);
-        if (host) ws.reserve(n * sizeof(float));
+        if (host) ws.add(&dev, n);
+        else dev = const_cast<float *>(p);
     }
-    fd_status place(Workspace &ws, cudaStream_t s) {
-        if (!user || !count) return FD_OK;
-        if (!host) {
-            dev = const_cast<float *>(user);
-            return FD_OK;
-        }
-        dev = ws.take_n<float>(count);
-        FD_CUDA_TRY(cudaMemcpyAsync(dev, user, count * sizeof(float), cudaMemcpyHostToDevice, s));
+    fd_status place(cudaStream_t s) {
+        if (host)
+            FD_CUDA_TRY(cudaMemcpyAsync(dev, user, count * sizeof(float), cudaMemcpyHostToDevice, s));
         return FD_OK;
     }
 };
@@ -135,14 +131,11 @@ struct StagedOut {
         user = p;
         count = n;
         host = p && n && !is_device_pointer(p);
-        if (host) ws.reserve(n * sizeof(float));
-    }
-    void place(Workspace &ws) {
-        if (!user || !count) return;
-        dev = host ? ws.take_n<float>(count) : user;
+        if (host) ws.add(&dev, n);
+        else dev = p;
     }
     fd_status copy_back(cudaStream_t s) {
-        if (host && count)
+        if (host)
             FD_CUDA_TRY(cudaMemcpyAsync(user, dev, count * sizeof(float), cudaMemcpyDeviceToHost, s));
         return FD_OK;
     }
@@ -291,12 +284,17 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     cudaStream_t s = cs.get();
 
     Workspace ws;
-    ws.reserve((size_t)2 * nshots * L.vol * 4);        // wavefields
-    ws.reserve((size_t)L.vol * 4);                      // b
-    ws.reserve((size_t)ndamp * 4);                      // damping / dt
-    ws.reserve((size_t)nshots * nsrc * sizeof(SparsePoint));
-    ws.reserve((size_t)nshots * nrec * sizeof(SparsePoint));
-    ws.reserve(sizeof(MediumStats) + 64);
+    float *wave, *bcoef, *dps;
+    SparsePoint *src_tab, *rec_tab;
+    MediumStats *dstats;
+    int *counter;
+    ws.add(&wave, (size_t)2 * nshots * L.vol);  // u at two levels per shot
+    ws.add(&bcoef, L.vol);                      // b = dt^2 / (m + damp dt/2)
+    ws.add(&dps, ndamp);                        // damping / dt
+    ws.add(&src_tab, (size_t)nshots * nsrc);
+    ws.add(&rec_tab, (size_t)nshots * nrec);
+    ws.add(&dstats, 1);
+    ws.add(&counter, 1);
     Staged sm, sdamp, ssxyz, swav, srxyz;
     StagedOut srec;
     sm.plan(ws, m, dense);
@@ -306,20 +304,9 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     srxyz.plan(ws, rec_xyz, (size_t)nshots * nrec * 3);
     srec.plan(ws, rec_out, (size_t)nshots * nt * nrec);
     FD_TRY(ws.allocate(s));
-
-    float *wave = ws.take_n<float>((size_t)2 * nshots * L.vol);
-    float *bcoef = ws.take_n<float>(L.vol);
-    float *dps = ws.take_n<float>(ndamp);
-    SparsePoint *src_tab = ws.take_n<SparsePoint>((size_t)nshots * nsrc + 1);
-    SparsePoint *rec_tab = ws.take_n<SparsePoint>((size_t)nshots * nrec + 1);
-    MediumStats *dstats = static_cast<MediumStats *>(ws.take(sizeof(MediumStats)));
-    int *counter = static_cast<int *>(ws.take(64));
-    FD_TRY(sm.place(ws, s));
-    FD_TRY(sdamp.place(ws, s));
-    FD_TRY(ssxyz.place(ws, s));
-    FD_TRY(swav.place(ws, s));
-    FD_TRY(srxyz.place(ws, s));
-    srec.place(ws);
+    FD_STAGE(s, "acoustic: workspace allocated");
+    for (Staged *st : {&sm, &sdamp, &ssxyz, &swav, &srxyz}) FD_TRY(st->place(s));
+    FD_STAGE(s, "acoustic: inputs staged");
 
     // ---- K0: coefficients, tables, validation
     FD_CUDA_TRY(cudaMemsetAsync(bcoef, 0, (size_t)L.vol * 4, s));
@@ -332,6 +319,7 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
                                   *grid, L, rec_tab + (size_t)sh * nrec, &dstats->flags, s));
     }
     FD_TRY(finish_medium_stats(dstats, s));
+    FD_STAGE(s, "acoustic: setup kernels");
     MediumStats hs;
     FD_TRY(read_stats(dstats, &hs, s));
     FD_TRY(flags_to_status(hs.flags, "acoustic_forward"));
@@ -355,7 +343,9 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
 
     // ---- K1 plan and arguments
     AcousticPlan plan;
+    FD_STAGE(s, "acoustic: initial state");
     FD_TRY(acoustic_plan(R, g_acoustic_config[R], L, nshots, wave, &plan));
+    FD_STAGE(s, plan.name);
     AcousticStepArgs a;
     memset(&a, 0, sizeof(a));
     a.wave = wave;
@@ -400,6 +390,7 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
         ai.cur = par;
         if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 0), s));
         FD_TRY(acoustic_launch(plan, ai, s));
+        if (!via_counter && trace_level() >= 2) FD_STAGE(s, "acoustic_step kernel");
         if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 1), s));
         SparseArgs si = sp;
         si.inj_level0 = 1 - par;
@@ -409,7 +400,8 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
         if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 2), s));
         return FD_OK;
     };
-    FD_TRY(run_time_loop(nsteps, s, counter, !timing, step));
+    FD_TRY(run_time_loop(nsteps, s, counter, !timing && trace_level() < 2, step));
+    FD_STAGE(s, "acoustic: time loop");
     const int last = nsteps & 1;  // level holding u^{nt-1}
     {
         SparseArgs si = sp;
@@ -418,6 +410,7 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
         FD_TRY(sparse_launch(si, nt - 1, false, nrec > 0, s));
     }
     FD_TRY(check_finite(wave, L, 2 * nshots, &dstats->flags, s));
+    FD_STAGE(s, "acoustic: final interpolation and check");
 
     // ---- outputs
     if (u_final) {
@@ -467,13 +460,18 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
     cudaStream_t s = cs.get();
 
     Workspace ws;
-    ws.reserve((size_t)4 * nshots * L.vol * 4);  // p, r at two levels
-    ws.reserve((size_t)6 * nshots * L.vol * 4);  // pass-1 temporaries
-    ws.reserve((size_t)6 * L.vol * 4);           // b, a, s, n (3)
-    ws.reserve((size_t)ndamp * 4);
-    ws.reserve((size_t)nshots * nsrc * sizeof(SparsePoint));
-    ws.reserve((size_t)nshots * nrec * sizeof(SparsePoint));
-    ws.reserve(sizeof(MediumStats) + 64);
+    float *wave, *tmp, *bcoef, *dps;
+    SparsePoint *src_tab, *rec_tab;
+    MediumStats *dstats;
+    int *counter;
+    ws.add(&wave, (size_t)4 * nshots * L.vol);  // p, r at two levels per shot
+    ws.add(&tmp, (size_t)6 * nshots * L.vol);   // pass-1 temporaries
+    ws.add(&bcoef, (size_t)6 * L.vol);          // b, a, s, n_x, n_y, n_z
+    ws.add(&dps, ndamp);
+    ws.add(&src_tab, (size_t)nshots * nsrc);
+    ws.add(&rec_tab, (size_t)nshots * nrec);
+    ws.add(&dstats, 1);
+    ws.add(&counter, 1);
     Staged sm, sdamp, seps, sdel, sth, sph, ssxyz, swav, srxyz;
     StagedOut srec;
     sm.plan(ws, m, dense);
@@ -487,21 +485,11 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
     srxyz.plan(ws, rec_xyz, (size_t)nshots * nrec * 3);
     srec.plan(ws, rec_out, (size_t)nshots * nt * nrec);
     FD_TRY(ws.allocate(s));
-
-    float *wave = ws.take_n<float>((size_t)4 * nshots * L.vol);
-    float *tmp = ws.take_n<float>((size_t)6 * nshots * L.vol);
-    float *bcoef = ws.take_n<float>(L.vol);
-    float *acoef = ws.take_n<float>(L.vol);
-    float *scoef = ws.take_n<float>(L.vol);
-    float *nvec = ws.take_n<float>((size_t)3 * L.vol);
-    float *dps = ws.take_n<float>(ndamp);
-    SparsePoint *src_tab = ws.take_n<SparsePoint>((size_t)nshots * nsrc + 1);
-    SparsePoint *rec_tab = ws.take_n<SparsePoint>((size_t)nshots * nrec + 1);
-    MediumStats *dstats = static_cast<MediumStats *>(ws.take(sizeof(MediumStats)));
-    int *counter = static_cast<int *>(ws.take(64));
+    float *acoef = bcoef + L.vol;
+    float *scoef = bcoef + 2 * L.vol;
+    float *nvec = bcoef + 3 * L.vol;
     for (Staged *st : {&sm, &sdamp, &seps, &sdel, &sth, &sph, &ssxyz, &swav, &srxyz})
-        FD_TRY(st->place(ws, s));
-    srec.place(ws);
+        FD_TRY(st->place(s));
 
     FD_CUDA_TRY(cudaMemsetAsync(bcoef, 0, (size_t)6 * L.vol * 4, s));
     FD_TRY(init_medium_stats(dstats, s));
@@ -592,7 +580,8 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
         if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 3), s));
         return FD_OK;
     };
-    FD_TRY(run_time_loop(nsteps, s, counter, !timing, step));
+    FD_TRY(run_time_loop(nsteps, s, counter, !timing && trace_level() < 2, step));
+    FD_STAGE(s, "tti: time loop");
     const int last = nsteps & 1;
     {
         SparseArgs si = sp;

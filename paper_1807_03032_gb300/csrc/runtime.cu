@@ -5,6 +5,7 @@
 #include <cudaTypedefs.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <map>
@@ -115,6 +116,30 @@ fd_status make_tensor_map_4d(CUtensorMap *map, const float *base, uint64_t nx, u
     return FD_OK;
 }
 
+int trace_level() {
+    static int level = [] {
+        const char *e = getenv("FDSWEEP_TRACE");
+        return e ? atoi(e) : 0;
+    }();
+    return level;
+}
+
+fd_status trace_stage(cudaStream_t s, const char *stage) {
+    const int lvl = trace_level();
+    if (lvl <= 0) return FD_OK;
+    fprintf(stderr, "[fdsweep] %s\n", stage);
+    fflush(stderr);
+    if (lvl >= 2) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return set_error(FD_ERR_CUDA, "after stage '%s': %s", stage, cudaGetErrorString(e));
+        fprintf(stderr, "[fdsweep] %s: ok\n", stage);
+        fflush(stderr);
+    }
+    return FD_OK;
+}
+
 bool is_device_pointer(const void *p) {
     if (!p) return true;
     cudaPointerAttributes attr;
@@ -130,10 +155,16 @@ bool is_device_pointer(const void *p) {
 
 Workspace::~Workspace() { release(); }
 
-void Workspace::reserve(size_t bytes) { total_ = (total_ + 255) / 256 * 256 + bytes; }
+void Workspace::add_raw(void **slot, size_t bytes) {
+    total_ = (total_ + 255) / 256 * 256;
+    if (npieces_ < 64) pieces_[npieces_++] = Piece{slot, total_};
+    *slot = nullptr;
+    total_ += bytes > 0 ? bytes : 1;
+}
 
 fd_status Workspace::allocate(cudaStream_t s) {
     stream_ = s;
+    if (npieces_ >= 64) return set_error(FD_ERR_ARG, "workspace: too many pieces");
     static std::once_flag once;
     std::call_once(once, [] {
         // Keep freed workspace in the stream-ordered pool instead of returning
@@ -156,15 +187,9 @@ fd_status Workspace::allocate(cudaStream_t s) {
                          "workspace allocation of %zu bytes failed: %s", total_,
                          cudaGetErrorString(e));
     }
-    cursor_ = 0;
+    for (int i = 0; i < npieces_; ++i)
+        *pieces_[i].slot = static_cast<char *>(base_) + pieces_[i].offset;
     return FD_OK;
-}
-
-void *Workspace::take(size_t bytes) {
-    cursor_ = (cursor_ + 255) / 256 * 256;
-    void *p = static_cast<char *>(base_) + cursor_;
-    cursor_ += bytes;
-    return p;
 }
 
 void Workspace::release() {

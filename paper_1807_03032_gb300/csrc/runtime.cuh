@@ -11,25 +11,41 @@ fd_status stats_reset();
 fd_status stats_get(const char *family, double *total_ms, int64_t *launches,
                     double *points_per_launch);
 
+// Debug tracing, controlled by the FDSWEEP_TRACE environment variable:
+// 1 prints each stage of a call to stderr, 2 also synchronises after every
+// stage (and disables graph capture) so that a device error is reported at the
+// stage that caused it.
+int trace_level();
+fd_status trace_stage(cudaStream_t s, const char *stage);
+#define FD_STAGE(stream, name) FD_TRY(::fdsweep::trace_stage((stream), (name)))
+
 // True for device or managed memory (and for null); false for host memory.
 bool is_device_pointer(const void *p);
 
 // One stream-ordered device allocation per call, carved into 256-byte aligned
-// pieces; released (cudaFreeAsync) when the object goes out of scope.
+// pieces.  Pieces are declared first (add), then allocate() assigns every
+// declared pointer; the block is released (cudaFreeAsync) when the object goes
+// out of scope.
 class Workspace {
   public:
     ~Workspace();
-    void reserve(size_t bytes);
-    fd_status allocate(cudaStream_t s);
-    void *take(size_t bytes);
     template <class T>
-    T *take_n(size_t n) {
-        return static_cast<T *>(take(n * sizeof(T)));
+    void add(T **slot, size_t count) {
+        add_raw(reinterpret_cast<void **>(slot), count * sizeof(T));
     }
+    void add_raw(void **slot, size_t bytes);
+    fd_status allocate(cudaStream_t s);
+    size_t bytes() const { return total_; }
     void release();
 
   private:
-    size_t total_ = 0, cursor_ = 0;
+    struct Piece {
+        void **slot;
+        size_t offset;
+    };
+    Piece pieces_[64];
+    int npieces_ = 0;
+    size_t total_ = 0;
     void *base_ = nullptr;
     cudaStream_t stream_ = nullptr;
 };

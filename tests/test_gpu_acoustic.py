@@ -240,8 +240,10 @@ def test_full_size_parity_first_steps():
 
 def test_full_size_full_run_is_linear_in_the_source():
     """512^3, so = 8, the full 1000 ms (594 steps): doubling the wavelet doubles
-    every trace sample exactly (FP32 scaling by 2 is exact), and the field
-    stays finite."""
+    every trace sample (exactly for normal numbers, since FP32 scaling by 2 is
+    exact; the stencil's numerical precursor ahead of the wavefront decays into
+    subnormals, where rounding is absolute and the factor 2 holds only to
+    2^-149), and the field stays finite."""
     torch = require_cuda()
     import paper_1807_03032_gb300 as fd
     w = workloads.acoustic_large(n=512, so=8)
@@ -253,5 +255,7 @@ def test_full_size_full_run_is_linear_in_the_source():
     torch.cuda.synchronize()
     assert torch.isfinite(rec1).all()
     assert float(rec1.abs().max()) > 0
-    assert torch.equal(rec2, 2 * rec1)
+    normal = rec1.abs() >= 1.2e-38
+    assert torch.equal(rec2[normal], 2 * rec1[normal])
+    assert float((rec2 - 2 * rec1).abs().max()) <= 1e-37
     assert w.nt == 594 and math.isclose(w.dt, 0.38 * 20.0 / 4.5)
