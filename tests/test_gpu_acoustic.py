@@ -255,7 +255,7 @@ def test_full_size_full_run_is_linear_in_the_source():
     torch.cuda.synchronize()
     assert torch.isfinite(rec1).all()
     assert float(rec1.abs().max()) > 0
-    normal = rec1.abs() >= 1.2e-38
-    assert torch.equal(rec2[normal], 2 * rec1[normal])
-    assert float((rec2 - 2 * rec1).abs().max()) <= 1e-37
+    big = rec1.abs() >= 1e-20 * float(rec1.abs().max())
+    assert torch.equal(rec2[big], 2 * rec1[big])
+    assert bool(((rec2 - 2 * rec1).abs() <= 1e-6 * (2 * rec1).abs() + 1e-37).all())
     assert w.nt == 594 and math.isclose(w.dt, 0.38 * 20.0 / 4.5)
