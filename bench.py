@@ -1,0 +1,467 @@
+"""Benchmark of the acoustic FD sweep on GB300 (one JSON line on rank 0).
+
+Workload (one benchmark "step"): the isotropic acoustic forward model on a
+512^3 grid (h = 20 m, smooth-random velocity 1.5-4.5 km/s from seeded noise
+with a 12-point Gaussian filter, 40-point absorbing border, one Ricker source,
+512 x 512 receivers half a cell below the border, 1000 ms = 594 steps at the
+CFL-limited dt) run once at each space order 4, 8, 12 and 16.  Metric:
+grid-point updates per second (GPts/s) over the whole C-ABI calls, inputs
+resident in HBM.  Every field is 512 MiB, larger than the 126 MB L2, so no L2
+flush is needed between steps.
+
+Also reported: the dominant kernel's roofline (acoustic_step, 16 algorithmic
+bytes per point: read u^n, u^{n-1}, b; write u^{n+1}), the same metric end to
+end with pinned host buffers (e2e), the FP64 CPU oracle on a bounded sample of
+the workload (cpu_baseline), TTI throughput on the 512^3 TTI workload, SM
+clocks sampled during the timed region and the number of kernel launches.
+
+``--impl reference`` times the FP64 CPU oracle instead (the reference arm):
+each step is one time step of the same 512^3 workload at each space order.
+
+Multi-GPU (torchrun, one rank per GPU): shots are independent, so each rank
+runs its own shot with no data-path collective (weak scaling); the timed
+region is bracketed by barriers and the maximum over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+SO_LIST = (4, 8, 12, 16)
+BYTES_PER_POINT_ACOUSTIC = 16.0  # read u^n, u^{n-1}, b; write u^{n+1}
+BYTES_PER_POINT_TTI = 44.0       # p, r: read 2 levels + write 1 (24 B); m, eps, delta, theta, phi (20 B)
+METRIC = "GPts/s (acoustic 512^3, so 4/8/12/16)"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return float(d["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("acoustic.cu", "kernels.cuh", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1807_03032_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """Per-launch DRAM bytes of acoustic_step from the committed ncu summary,
+    or None if the kernel source changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "acoustic_step_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get("kernel_hash") != kernel_source_hash():
+        return None
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            for name, v in zip(names, r[2:]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def build_workload(rank, n, so):
+    w = workloads.acoustic_large(n=n, so=so, nt=None)
+    if rank:
+        # each rank models its own shot: shift the source along x
+        w.src_xyz[..., 0] += np.float32(rank * 7 * w.spacing[0])
+    return w
+
+
+def run_ours(args):
+    import torch
+    import paper_1807_03032_gb300 as fd
+    from paper_1807_03032_gb300 import _native
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    _native.load()
+
+    n = args.n
+    t0 = time.time()
+    w = build_workload(rank, n, SO_LIST[0])
+    log(f"[bench] workload built in {time.time() - t0:.1f}s: {w.name}, nt={w.nt}, dt={w.dt:.4f} ms")
+    g = fd.Grid(w.shape, w.spacing, w.origin)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    m, damp, sxyz, swav, rxyz = T(w.m), T(w.damp), T(w.src_xyz), T(w.src_wav), T(w.rec_xyz)
+    nrec = rxyz.shape[1]
+    rec_out = torch.empty((1, w.nt, nrec), dtype=torch.float32, device=dev)
+    points_per_forward = float(w.npoints) * (w.nt - 1) * w.nshots
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for so in args.so:
+            fd.acoustic_forward(g, so, w.dt, w.nt, m, sxyz, swav, rxyz, damp=damp,
+                                rec_out=rec_out, return_final=False)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---------------------------------------------------------------- timed region
+    _native.stats_reset()
+    _native.stats_enable(True)
+    launches0 = _native.launch_count()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    per_so_ms = {so: 0.0 for so in args.so}
+    for _ in range(args.steps):
+        for so in args.so:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fd.acoustic_forward(g, so, w.dt, w.nt, m, sxyz, swav, rxyz, damp=damp,
+                                rec_out=rec_out, return_final=False)
+            e1.record(stream)
+            e1.synchronize()
+            per_so_ms[so] += e0.elapsed_time(e1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    launches = _native.launch_count() - launches0
+    k1_ms, k1_n, k1_pts = _native.stats_get("acoustic_step")
+    sp_ms, sp_n, _ = _native.stats_get("sparse")
+    _native.stats_enable(False)
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    total_points = points_per_forward * len(args.so) * args.steps * ws
+    value = total_points / (elapsed_ms * 1e-3) / 1e9
+    ms_per_step = elapsed_ms / args.steps
+
+    # per space order: whole-call GPts/s and kernel roofline (per-so stats)
+    per_so = {}
+    for so in args.so:
+        per_so[str(so)] = {"gpts": round(points_per_forward * args.steps / (per_so_ms[so] * 1e-3) / 1e9, 2)}
+    peak, peak_kind = measured_peaks()
+    k1_launch_ms = k1_ms / max(k1_n, 1)
+    achieved = BYTES_PER_POINT_ACOUSTIC * k1_pts / (k1_launch_ms * 1e-3) / 1e9
+    traffic = None
+    tr = ncu_traffic()
+    if tr:
+        vals = [tr["bytes_per_launch"].get(str(so)) for so in args.so]
+        if all(v is not None for v in vals):
+            traffic = float(np.mean(vals)) * (k1_pts / tr.get("points_per_launch", k1_pts))
+    roofline = {"bound": "hbm", "kernel": "acoustic_step", "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "bytes_per_point": BYTES_PER_POINT_ACOUSTIC,
+                "launch_ms": round(k1_launch_ms, 4), "launches": k1_n,
+                "sparse_launch_ms": round(sp_ms / max(sp_n, 1), 4)}
+
+    # per-so kernel rooflines (separate short timed passes, one forward each)
+    for so in args.so:
+        _native.stats_reset()
+        _native.stats_enable(True)
+        fd.acoustic_forward(g, so, w.dt, w.nt, m, sxyz, swav, rxyz, damp=damp, rec_out=rec_out,
+                            return_final=False)
+        ms_, n_, pts_ = _native.stats_get("acoustic_step")
+        _native.stats_enable(False)
+        a_ = BYTES_PER_POINT_ACOUSTIC * pts_ / (ms_ / n_ * 1e-3) / 1e9
+        per_so[str(so)].update({"kernel_gbs": round(a_, 1), "kernel_frac": round(a_ / peak, 4),
+                                "kernel_gpts": round(pts_ / (ms_ / n_ * 1e-3) / 1e9, 2)})
+
+    # ---------------------------------------------------------------- end to end (host buffers)
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        hm, hdamp, hs, hw, hr = pin(w.m), pin(w.damp), pin(w.src_xyz), pin(w.src_wav), pin(w.rec_xyz)
+        hrec = torch.empty((1, w.nt, nrec), dtype=torch.float32).pin_memory()
+        h2d = sum(t.numel() * 4 for t in (hm, hdamp, hs, hw, hr)) * len(args.so)
+        d2h = hrec.numel() * 4 * len(args.so)
+
+        def step_host():
+            for so in args.so:
+                fd.acoustic_forward(g, so, w.dt, w.nt, hm, hs, hw, hr, damp=hdamp, rec_out=hrec,
+                                    return_final=False, stream=stream.cuda_stream)
+
+        step_host()
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ksteps = max(1, min(args.steps, 3))
+        for _ in range(ksteps):
+            step_host()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e_ms = e0.elapsed_time(e1)
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": round(points_per_forward * len(args.so) * ksteps * ws / (e_ms * 1e-3) / 1e9, 2),
+               "unit": "GPts/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "steps": ksteps, "host_memory": "pinned"}
+
+    # ---------------------------------------------------------------- TTI
+    tti = None
+    if not args.no_tti:
+        del m, damp, sxyz, swav, rxyz, rec_out
+        torch.cuda.empty_cache()
+        tti = run_tti(args, fd, _native, dev, stream, peak)
+
+    # ---------------------------------------------------------------- CPU baseline (oracle)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.so)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "GPts/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"acoustic forward {n}^3, h=20 m, smooth-random v 1.5-4.5 km/s, "
+                                   f"40-pt border, 1 Ricker source, {n}x{n} receivers, "
+                                   f"nt={w.nt} (1000 ms), so in {list(args.so)}; one step = one "
+                                   "forward per space order",
+                       "grid": [n, n, n], "nt": w.nt, "so": list(args.so), "shots_per_gpu": 1,
+                       "parallelism": f"shots x {ws} (replicas, no collective)",
+                       "l2": "inputs larger than L2 (512 MiB per field); no flush",
+                       "timing": "CUDA events on the calling stream around whole C-ABI calls; "
+                                 "kernel times from the library's per-launch events"},
+            "per_so": per_so,
+            "roofline": roofline,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "tti": tti,
+            "clocks": clocks,
+            "gpu_launches": int(launches),
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_tti(args, fd, _native, dev, stream, peak):
+    import torch
+    n = args.n
+    t0 = time.time()
+    w = workloads.tti_large(n=n, so=4)
+    log(f"[bench] TTI workload built in {time.time() - t0:.1f}s, nt={w.nt}")
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    g = fd.Grid(w.shape, w.spacing, w.origin)
+    arrs = [T(a) for a in (w.m, w.eps, w.delta, w.theta, w.phi, w.src_xyz, w.src_wav, w.rec_xyz,
+                           w.damp)]
+    m, e, d, th, ph, sx, sw, rx, dd = arrs
+    rec = torch.empty((1, w.nt, rx.shape[1]), dtype=torch.float32, device=dev)
+    out = {"workload": f"TTI {n}^3 two-layer 1.5/2.5 km/s, eps U[0,0.3], delta U[0,0.2] "
+                       f"(<= eps), theta/phi smooth in [0, pi/4], nt={w.nt}",
+           "bytes_per_point": BYTES_PER_POINT_TTI, "per_so": {}}
+    pts = float(w.npoints) * (w.nt - 1)
+    for so in args.so:
+        fd.tti_forward(g, so, w.dt, 20, m, e, d, th, ph, sx, sw[:, :20].contiguous(), rx,
+                       damp=dd, rec_out=rec[:, :20].contiguous(), return_final=False)
+        _native.stats_reset()
+        _native.stats_enable(True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fd.tti_forward(g, so, w.dt, w.nt, m, e, d, th, ph, sx, sw, rx, damp=dd, rec_out=rec,
+                       return_final=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        p1 = _native.stats_get("tti_pass1")
+        p2 = _native.stats_get("tti_pass2")
+        _native.stats_enable(False)
+        kms = (p1[0] + p2[0]) / max(p1[1], 1)
+        gb = BYTES_PER_POINT_TTI * p1[2] / (kms * 1e-3) / 1e9
+        out["per_so"][str(so)] = {"gpts": round(pts / (ms * 1e-3) / 1e9, 2),
+                                  "step_kernel_ms": round(kms, 4),
+                                  "pass1_ms": round(p1[0] / max(p1[1], 1), 4),
+                                  "pass2_ms": round(p2[0] / max(p2[1], 1), 4),
+                                  "hbm_frac_44B": round(gb / peak, 4)}
+    return out
+
+
+def cpu_baseline(w, so_list):
+    """The FP64 oracle, as it stands, on the host cores: one time step of the
+    512^3 workload at each space order (a bounded sample of the workload)."""
+    import oracle
+    g = oracle.make_grid(w.shape, w.spacing, w.origin)
+    cores = os.cpu_count() or 1
+    t_total = 0.0
+    pts = 0.0
+    for so in so_list:
+        t0 = time.perf_counter()
+        oracle.acoustic_forward(g, so, w.dt, 2, w.m, w.src_xyz, w.src_wav[:, :2], w.rec_xyz,
+                                damp=w.damp)
+        t_total += time.perf_counter() - t0
+        pts += float(w.npoints)
+    return {"value": round(pts / t_total / 1e9, 4), "unit": "GPts/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"1 time step at each so in {list(so_list)} of the {w.shape[0]}^3 workload "
+                      "(FP64 C oracle, OpenMP over all host cores, setup included)",
+            "seconds": round(t_total, 2)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    n = args.n
+    w = build_workload(0, n, SO_LIST[0])
+    g = oracle.make_grid(w.shape, w.spacing, w.origin)
+    cores = os.cpu_count() or 1
+
+    def step():
+        for so in args.so:
+            oracle.acoustic_forward(g, so, w.dt, 2, w.m, w.src_xyz, w.src_wav[:, :2], w.rec_xyz,
+                                    damp=w.damp)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    t = time.perf_counter() - t0
+    pts = float(w.npoints) * len(args.so) * args.steps
+    value = pts / t / 1e9
+    sample = (f"each step = 1 time step of the {n}^3 acoustic workload at each so in "
+              f"{list(args.so)} (FP64 C oracle, OpenMP)")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GPts/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t / args.steps * 1e3, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"acoustic forward {n}^3, so in {list(args.so)}, sample of "
+                                   "the GPU arm's workload", "grid": [n, n, n]},
+            "cpu_baseline": {"value": round(value, 4), "unit": "GPts/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "GPts/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--so", type=int, nargs="+", default=list(SO_LIST))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tti", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.so = tuple(args.so)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

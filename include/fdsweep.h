@@ -149,6 +149,10 @@ fd_status fd_stats_reset(void);
 fd_status fd_stats_get(const char *family, double *total_ms, int64_t *launches,
                        double *points_per_launch);
 
+/* Number of kernel launches this library has enqueued since it was loaded
+ * (a replayed CUDA graph counts each of its kernel nodes). */
+int64_t fd_launch_count(void);
+
 /*
  * Tile configuration override for the acoustic stencil kernel (for tuning
  * sweeps): index into the compiled configuration table for the given space

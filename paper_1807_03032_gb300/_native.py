@@ -24,7 +24,7 @@ STATUS_NAMES = {
 # Every symbol include/fdsweep.h declares (checked by the ABI test).
 EXPORTED = ("acoustic_forward", "tti_forward", "fd_last_error", "fd_version",
             "fd_stats_enable", "fd_stats_reset", "fd_stats_get", "fd_set_acoustic_config",
-            "fd_num_acoustic_configs")
+            "fd_num_acoustic_configs", "fd_launch_count")
 
 
 class FdGrid(ctypes.Structure):
@@ -79,6 +79,8 @@ def load(path: str = LIB_PATH):
         lib.fd_set_acoustic_config.restype = I
         lib.fd_num_acoustic_configs.argtypes = [I]
         lib.fd_num_acoustic_configs.restype = I
+        lib.fd_launch_count.argtypes = []
+        lib.fd_launch_count.restype = ctypes.c_int64
         _lib = lib
         return lib
 
@@ -114,6 +116,11 @@ def stats_get(family: str):
     check(load().fd_stats_get(family.encode(), ctypes.byref(ms), ctypes.byref(n),
                               ctypes.byref(pts)))
     return ms.value, n.value, pts.value
+
+
+def launch_count() -> int:
+    """Kernel launches enqueued by the library since it was loaded."""
+    return int(load().fd_launch_count())
 
 
 def set_acoustic_config(so: int, config: int):

@@ -334,6 +334,7 @@ fd_status acoustic_launch(const AcousticPlan &plan, const AcousticStepArgs &args
     void *params[] = {(void *)&plan.map, (void *)&args, (void *)&zchunk, (void *)&nzc};
     FD_CUDA_TRY(cudaLaunchKernel(tab[plan.config].fn, plan.grid, plan.block, params, plan.smem,
                                  stream));
+    note_launch(stream);
     return FD_OK;
 }
 

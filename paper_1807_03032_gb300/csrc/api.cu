@@ -194,11 +194,13 @@ fd_status run_time_loop(int nsteps, cudaStream_t s, int *counter, bool allow_gra
         FD_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
+        take_captured();
         if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
             fd_status st = FD_OK;
             for (int i = 0; i < kGraphChunk && st == FD_OK; ++i) st = step(i, i & 1, true);
             if (st == FD_OK) st = bump_counter(counter, kGraphChunk, s);
             cudaError_t e = cudaStreamEndCapture(s, &graph);
+            const int64_t per_graph = take_captured();
             if (st != FD_OK) {
                 if (graph) cudaGraphDestroy(graph);
                 return st;
@@ -213,6 +215,7 @@ fd_status run_time_loop(int nsteps, cudaStream_t s, int *counter, bool allow_gra
                 if (e != cudaSuccess) break;
             }
             cudaGraphExecDestroy(exec);  // released once the queued launches complete
+            add_launches(per_graph * reps);
             FD_CUDA_TRY(e);
             n = reps * kGraphChunk;
         } else {
@@ -649,6 +652,8 @@ fd_status tti_forward(const fd_grid *grid, int so, double dt, int nt, int nshots
 }
 
 const char *fd_last_error(void) { return fdsweep::last_error(); }
+
+int64_t fd_launch_count(void) { return fdsweep::launch_count(); }
 
 const char *fd_version(void) { return "fdsweep 0.1 (sm_103a)"; }
 

@@ -50,6 +50,14 @@ fd_status make_tensor_map_4d(CUtensorMap *map, const float *base, uint64_t nx, u
                              uint64_t stride_z_bytes, uint64_t stride_w_bytes, uint32_t box_x,
                              uint32_t box_y, uint32_t box_z, uint32_t box_w);
 
+// Launch accounting (fd_launch_count): call note_launch(stream) after every
+// kernel launch.  Launches recorded while the stream is being captured are
+// counted when the graph is replayed (take_captured / add_launches).
+void note_launch(cudaStream_t s);
+int64_t take_captured();
+void add_launches(int64_t n);
+int64_t launch_count();
+
 // Kernel-timing statistics (see fd_stats_* in fdsweep.h).
 bool stats_enabled();
 void stats_add(const char *family, double ms, int64_t launches, double points_per_launch);

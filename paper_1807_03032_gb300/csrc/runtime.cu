@@ -8,6 +8,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -28,6 +29,29 @@ std::mutex g_stats_mu;
 std::map<std::string, StatEntry> g_stats;
 bool g_stats_on = false;
 }  // namespace
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+thread_local int64_t t_captured = 0;
+}  // namespace
+
+void note_launch(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusActive)
+        ++t_captured;
+    else
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+int64_t take_captured() {
+    const int64_t n = t_captured;
+    t_captured = 0;
+    return n;
+}
+
+void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 fd_status set_error(fd_status st, const char *fmt, ...) {
     va_list ap;

@@ -180,6 +180,7 @@ fd_status init_medium_stats(MediumStats *dev_stats, cudaStream_t stream) {
     static_assert(sizeof(StatsKeys) == sizeof(MediumStats), "stats layout");
     init_stats_kernel<<<1, 1, 0, stream>>>(reinterpret_cast<StatsKeys *>(dev_stats));
     FD_CUDA_TRY(cudaGetLastError());
+    note_launch(stream);
     return FD_OK;
 }
 
@@ -190,9 +191,11 @@ fd_status setup_acoustic_coeffs(const float *m, const float *damp, double dt,
     const int64_t n = (int64_t)L.nx * L.ny * L.nz;
     acoustic_coeff_kernel<<<grid_for(n, 256), 256, 0, stream>>>(m, damp, dt, L, bcoef, keys);
     FD_CUDA_TRY(cudaGetLastError());
+    note_launch(stream);
     const int nd = L.nx + L.ny + L.nz;
     damp_scale_kernel<<<(nd + 255) / 256, 256, 0, stream>>>(damp, nd, dt, dps);
     FD_CUDA_TRY(cudaGetLastError());
+    note_launch(stream);
     return FD_OK;
 }
 
@@ -204,6 +207,7 @@ fd_status setup_tti_coeffs(const float *eps, const float *delta, const float *th
     tti_coeff_kernel<<<grid_for(n, 256), 256, 0, stream>>>(eps, delta, theta, phi, L, acoef,
                                                            scoef, nvec, keys);
     FD_CUDA_TRY(cudaGetLastError());
+    note_launch(stream);
     return FD_OK;
 }
 
@@ -212,6 +216,7 @@ fd_status setup_sparse_table(const float *xyz, int npts, const fd_grid &g, const
     if (npts <= 0) return FD_OK;
     sparse_table_kernel<<<(npts + 255) / 256, 256, 0, stream>>>(xyz, npts, g, L, tab, flags);
     FD_CUDA_TRY(cudaGetLastError());
+    note_launch(stream);
     return FD_OK;
 }
 
@@ -220,6 +225,7 @@ fd_status check_finite(const float *field, const WaveLayout &L, int nfields, uns
     const int64_t n = L.vol * nfields;
     finite_kernel<<<grid_for(n, 256), 256, 0, stream>>>(field, n, flags);
     FD_CUDA_TRY(cudaGetLastError());
+    note_launch(stream);
     return FD_OK;
 }
 
@@ -227,6 +233,7 @@ fd_status check_finite(const float *field, const WaveLayout &L, int nfields, uns
 fd_status finish_medium_stats(MediumStats *dev_stats, cudaStream_t stream) {
     finish_stats_kernel<<<1, 1, 0, stream>>>(reinterpret_cast<StatsKeys *>(dev_stats));
     FD_CUDA_TRY(cudaGetLastError());
+    note_launch(stream);
     return FD_OK;
 }
 

@@ -72,12 +72,14 @@ fd_status sparse_launch(const SparseArgs &a, int step, bool do_inject, bool do_i
     sparse_kernel<<<(unsigned)blocks, threads, 0, stream>>>(a, step, do_inject ? 1 : 0,
                                                             nrec_total);
     FD_CUDA_TRY(cudaGetLastError());
+    note_launch(stream);
     return FD_OK;
 }
 
 fd_status bump_counter(int *counter, int by, cudaStream_t stream) {
     bump_kernel<<<1, 1, 0, stream>>>(counter, by);
     FD_CUDA_TRY(cudaGetLastError());
+    note_launch(stream);
     return FD_OK;
 }
 

@@ -101,9 +101,11 @@ fd_status launch_r(const TtiArgs &a, cudaStream_t stream, cudaEvent_t *ev) {
     if (ev) FD_CUDA_TRY(cudaEventRecord(ev[0], stream));
     tti_pass1_kernel<R><<<grid, block, 0, stream>>>(a);
     FD_CUDA_TRY(cudaGetLastError());
+    note_launch(stream);
     if (ev) FD_CUDA_TRY(cudaEventRecord(ev[1], stream));
     tti_pass2_kernel<R><<<grid, block, 0, stream>>>(a);
     FD_CUDA_TRY(cudaGetLastError());
+    note_launch(stream);
     if (ev) FD_CUDA_TRY(cudaEventRecord(ev[2], stream));
     return FD_OK;
 }
