@@ -9,15 +9,24 @@
 // damp (u+ - u-)/(2 dt) = lap(u) rearranged for u+; with damp = 0 it is
 // u+ = 2u - u- + dt^2 lap(u) / m.
 //
-// GB300 design: one CTA owns a BX x BY column of the grid and marches it
-// through z.  Each xy plane of u^n (tile plus an R-wide halo, zero-filled
-// outside the grid by the TMA unit) is staged into a ring of shared-memory
-// stages by cp.async.bulk.tensor, D planes ahead of use, completing on one
-// mbarrier per stage.  Every thread owns a 4 (x, one float4) by VY (y)
-// micro-tile; the z-neighbours live in a register queue of 2R+1 planes, the x-
-// and y-neighbours are read from the staged plane.  u^{n-1} and b stream in
-// with float4 loads, u^{n+1} overwrites u^{n-1} in place.  Algorithmic HBM
-// traffic: 16 bytes per point (read u^n, u^{n-1}, b; write u^{n+1}).
+// GB300 design.  One CTA owns a BX x BY column of the grid and marches it
+// through z.  Every plane p of u^n (tile plus an R-wide halo, zero-filled
+// outside the grid by the TMA unit) is brought into a small ring of shared-
+// memory stages by cp.async.bulk.tensor, D planes ahead of use; the same stage
+// also receives the interior tiles of u^n, u^{n-1} and b for the output plane
+// p - R.  Each stage has a "full" mbarrier (TMA transaction count) and an
+// "empty" mbarrier (one arrival per warp), so warps run decoupled and thread 0
+// refills a stage as soon as every warp has released it.
+//
+// The z-direction uses an accumulator pipeline: when plane p arrives, each
+// thread adds w_|p-z| u(p) to the 2R pending outputs z in [p-R, p+R) it holds
+// in registers, adds the x/y part of the Laplacian of plane p (read from the
+// staged plane) to output p, and completes output p-R.  Per point this keeps
+// 2R floats of state (instead of a 2R+1-plane queue plus R staged planes), so
+// the shared-memory ring is only D+1 planes deep.  Every thread owns a 4 (x,
+// one float4) by VY (y) micro-tile.  Algorithmic HBM traffic: 16 bytes per
+// point (read u^n, u^{n-1}, b; write u^{n+1}); halo and centre re-reads are
+// served by L2.
 #include <stdio.h>
 
 #include "kernels.cuh"
@@ -32,53 +41,81 @@ struct AcCfg {
     static constexpr int RA = (R + 3) / 4 * 4;  // x halo rounded to 16 bytes (TMA rule)
     static constexpr int PW = BX + 2 * RA;
     static constexpr int PH = BY + 2 * R;
-    static constexpr int NS = R + D + 1;        // stages: R+1 planes in use + D in flight
-    static constexpr int STAGE = (PW * PH + 31) / 32 * 32;
-    static constexpr uint32_t BYTES = PW * PH * 4;
-    // stages, then NS mbarriers and an abort flag; +128 bytes to align the base
-    static constexpr size_t SMEM = (size_t)NS * STAGE * 4 + NS * 8 + 16 + 128;
+    static constexpr int NSL = D + 1;           // ring slots
+    static constexpr int HALO = (PW * PH + 31) / 32 * 32;
+    static constexpr int INT = BX * BY;         // interior tile (multiple of 32)
+    static constexpr int STAGE = HALO + 3 * INT;  // [halo u^n][u^n][u^{n-1}][b]
+    static constexpr uint32_t HALO_BYTES = PW * PH * 4;
+    static constexpr uint32_t INT_BYTES = INT * 4;
     static constexpr int THREADS = TX * TY;
-    static_assert(PW <= 256 && PH <= 256, "TMA box dimension limit");
+    static constexpr int WARPS = THREADS / 32;
+    static constexpr size_t SMEM = (size_t)NSL * STAGE * 4 + NSL * 16 + 16 + 128;
+    static_assert(PW <= 256 && PH <= 256 && BX <= 256 && BY <= 256, "TMA box dimension limit");
+    static_assert(INT % 32 == 0 && THREADS % 32 == 0, "tile shape");
 };
 
 template <int R, int TX, int TY, int VY, int D>
 __global__ void __launch_bounds__(TX *TY)
-    acoustic_step_kernel(const __grid_constant__ CUtensorMap map, const AcousticStepArgs a,
+    acoustic_step_kernel(const __grid_constant__ CUtensorMap map_halo,
+                         const __grid_constant__ CUtensorMap map_int,
+                         const __grid_constant__ CUtensorMap map_b, const AcousticStepArgs a,
                          int zchunk, int nzc) {
     using C = AcCfg<R, TX, TY, VY, D>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    // TMA destinations: 128-byte aligned stages of STAGE floats each
     float *smem = reinterpret_cast<float *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::NS * C::STAGE);
-    volatile int &s_abort = *reinterpret_cast<volatile int *>(bars + C::NS);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::NSL * C::STAGE);
+    uint64_t *empty = full + C::NSL;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + C::NSL);
 
     const int tid = threadIdx.x;
+    const int lane = tid & 31;
     const int tx = tid % TX, ty = tid / TX;
     const int shot = blockIdx.z / nzc;
     const int chunk = blockIdx.z - shot * nzc;
     const int x0 = blockIdx.x * C::BX, y0 = blockIdx.y * C::BY;
     const int za = chunk * zchunk;
     const int zb = min(a.L.nz, za + zchunk);
-    const int nplanes = zb - za + 2 * R;  // planes za-R .. zb+R-1
-    const int wcur = 2 * shot + a.cur;
+    const int nplanes = zb - za + 2 * R;  // arriving planes za-R .. zb+R-1
+    const int wcur = 2 * shot + a.cur, wprev = 2 * shot + 1 - a.cur;
     const int gx = x0 + 4 * tx;
 
     if (tid == 0) {
-        prefetch_tensormap(&map);
-        for (int s = 0; s < C::NS; ++s) mbar_init(&bars[s], 1);
+        prefetch_tensormap(&map_halo);
+        prefetch_tensormap(&map_int);
+        prefetch_tensormap(&map_b);
+        for (int s = 0; s < C::NSL; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], C::WARPS);
+        }
         fence_mbar_init();
-        s_abort = 0;
+        *abort_flag = 0;
     }
     __syncthreads();
 
-    if (tid == 0) {
-        for (int j = 0; j < D && j < nplanes; ++j) {
-            mbar_arrive_expect_tx(&bars[j], C::BYTES);
-            tma_load_4d(smem + j * C::STAGE, &map, &bars[j], x0 - C::RA, y0 - R, za - R + j,
-                        wcur);
+    // Producer (thread 0): stage for iteration jj = halo plane za-R+jj, plus
+    // the interior tiles of output plane za-2R+jj once jj >= 2R.
+    int issued = 0;
+    auto issue = [&](int jj) -> bool {
+        const int slot = jj % C::NSL;
+        if (jj >= C::NSL &&
+            !mbar_wait_bounded(&empty[slot], (uint32_t)(((jj - C::NSL) / C::NSL) & 1)))
+            return false;
+        const bool with_out = jj >= 2 * R;
+        mbar_arrive_expect_tx(&full[slot], C::HALO_BYTES + (with_out ? 3 * C::INT_BYTES : 0));
+        float *st = smem + slot * C::STAGE;
+        tma_load_4d(st, &map_halo, &full[slot], x0 - C::RA, y0 - R, za - R + jj, wcur);
+        if (with_out) {
+            const int zo = za - 2 * R + jj;
+            tma_load_4d(st + C::HALO, &map_int, &full[slot], x0, y0, zo, wcur);
+            tma_load_4d(st + C::HALO + C::INT, &map_int, &full[slot], x0, y0, zo, wprev);
+            tma_load_4d(st + C::HALO + 2 * C::INT, &map_b, &full[slot], x0, y0, zo, 0);
         }
-    }
+        issued = jj + 1;
+        return true;
+    };
+    if (tid == 0)
+        for (int jj = 0; jj < D && jj < nplanes; ++jj) issue(jj);
 
     const bool xok = gx < a.L.nxp;
     float dpx4[4];
@@ -93,141 +130,154 @@ __global__ void __launch_bounds__(TX *TY)
         yok[v] = gy[v] < a.L.ny;
         dpyv[v] = yok[v] ? a.dpy[gy[v]] : 0.f;
     }
-    float *__restrict__ unew = a.wave + (int64_t)(2 * shot + 1 - a.cur) * a.L.vol;
+    float *__restrict__ unew = a.wave + (int64_t)wprev * a.L.vol;
 
-    float4 q[2 * R + 1][VY];
+    // acc[i][v]: pending output plane p - R + i (p = arriving plane)
+    float4 acc[2 * R][VY];
 #pragma unroll
-    for (int s = 0; s < 2 * R + 1; ++s)
+    for (int i = 0; i < 2 * R; ++i)
 #pragma unroll
-        for (int v = 0; v < VY; ++v) q[s][v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int v = 0; v < VY; ++v) acc[i][v] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-    int j = 0;
-    for (; j < nplanes; ++j) {
-        const int zo = za + j - 2 * R;  // output plane completed by this iteration
-        const bool has_out = j >= 2 * R;
-        float4 um[VY], bb[VY];
+    bool failed = false;
+    for (int j = 0; j < nplanes; ++j) {
+        if (tid == 0 && j + D < nplanes && !failed) {
+            if (!issue(j + D)) {
+                failed = true;
+                *abort_flag = 1;
+                atomicOr(a.err, DEV_ERR_TIMEOUT);
+            }
+        }
+        const int slot = j % C::NSL;
+        if (*abort_flag || !mbar_wait_bounded(&full[slot], (uint32_t)((j / C::NSL) & 1))) {
+            *abort_flag = 1;
+            atomicOr(a.err, DEV_ERR_TIMEOUT);
+            break;
+        }
+        const float *H = smem + slot * C::STAGE;
+        const int rbase = R + ty * VY;
+
+        // x/y part of the Laplacian of plane p (centre weight of all axes
+        // included) and the centre values
+        float4 cen[VY], lxy[VY];
 #pragma unroll
         for (int v = 0; v < VY; ++v) {
-            um[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-            bb[v] = um[v];
-            if (has_out && xok && yok[v]) {
-                const int64_t off = (int64_t)zo * a.L.plane + (int64_t)gy[v] * a.L.nxp + gx;
-                um[v] = *reinterpret_cast<const float4 *>(unew + off);
-                bb[v] = ld_nc_f4(a.bcoef + off);
+            float xs[2 * C::RA + 4];
+            const float *row = H + (rbase + v) * C::PW + 4 * tx;
+#pragma unroll
+            for (int t = 0; t < (2 * C::RA + 4) / 4; ++t) {
+                const float4 f = *reinterpret_cast<const float4 *>(row + 4 * t);
+                xs[4 * t + 0] = f.x;
+                xs[4 * t + 1] = f.y;
+                xs[4 * t + 2] = f.z;
+                xs[4 * t + 3] = f.w;
+            }
+            const float4 c = make_float4(xs[C::RA], xs[C::RA + 1], xs[C::RA + 2], xs[C::RA + 3]);
+            float4 s;
+            s.x = a.wc * c.x;
+            s.y = a.wc * c.y;
+            s.z = a.wc * c.z;
+            s.w = a.wc * c.w;
+#pragma unroll
+            for (int k = 1; k <= R; ++k) {
+                s.x = fmaf(a.wx[k], xs[C::RA + 0 + k] + xs[C::RA + 0 - k], s.x);
+                s.y = fmaf(a.wx[k], xs[C::RA + 1 + k] + xs[C::RA + 1 - k], s.y);
+                s.z = fmaf(a.wx[k], xs[C::RA + 2 + k] + xs[C::RA + 2 - k], s.z);
+                s.w = fmaf(a.wx[k], xs[C::RA + 3 + k] + xs[C::RA + 3 - k], s.w);
+            }
+            cen[v] = c;
+            lxy[v] = s;
+        }
+#pragma unroll
+        for (int dy = -R; dy < VY + R; ++dy) {
+            bool needed = false;
+#pragma unroll
+            for (int v = 0; v < VY; ++v) {
+                const int k = dy > v ? dy - v : v - dy;
+                if (k >= 1 && k <= R) needed = true;
+            }
+            if (!needed) continue;
+            const float4 f =
+                *reinterpret_cast<const float4 *>(H + (rbase + dy) * C::PW + C::RA + 4 * tx);
+#pragma unroll
+            for (int v = 0; v < VY; ++v) {
+                const int k = dy > v ? dy - v : v - dy;
+                if (k >= 1 && k <= R) {
+                    lxy[v].x = fmaf(a.wy[k], f.x, lxy[v].x);
+                    lxy[v].y = fmaf(a.wy[k], f.y, lxy[v].y);
+                    lxy[v].z = fmaf(a.wy[k], f.z, lxy[v].z);
+                    lxy[v].w = fmaf(a.wy[k], f.w, lxy[v].w);
+                }
             }
         }
-        if (tid == 0 && j + D < nplanes) {
-            const int jj = j + D;
-            const int slot = jj % C::NS;
-            mbar_arrive_expect_tx(&bars[slot], C::BYTES);
-            tma_load_4d(smem + slot * C::STAGE, &map, &bars[slot], x0 - C::RA, y0 - R,
-                        za - R + jj, wcur);
-        }
-        const int slot = j % C::NS;
-        const bool ok = mbar_wait_bounded(&bars[slot], (uint32_t)((j / C::NS) & 1));
-        if (!ok) {
-            s_abort = 1;
-            atomicOr(a.err, DEV_ERR_TIMEOUT);
-        } else {
-#pragma unroll
-            for (int s = 0; s < 2 * R; ++s)
-#pragma unroll
-                for (int v = 0; v < VY; ++v) q[s][v] = q[s + 1][v];
-            const float *P = smem + slot * C::STAGE;
-#pragma unroll
-            for (int v = 0; v < VY; ++v)
-                q[2 * R][v] = *reinterpret_cast<const float4 *>(
-                    P + (R + ty * VY + v) * C::PW + C::RA + 4 * tx);
 
-            if (has_out) {
-                const float *Cp = smem + ((j - R) % C::NS) * C::STAGE;
-                const int rbase = R + ty * VY;
-                float4 acc[VY];
+        // z part: plane p feeds the pending outputs p-R .. p+R-1 and starts p+R
 #pragma unroll
-                for (int v = 0; v < VY; ++v) {
-                    const float4 c = q[R][v];
-                    float4 s;
-                    s.x = a.wc * c.x;
-                    s.y = a.wc * c.y;
-                    s.z = a.wc * c.z;
-                    s.w = a.wc * c.w;
+        for (int v = 0; v < VY; ++v) {
+            const float4 c = cen[v];
 #pragma unroll
-                    for (int k = 1; k <= R; ++k) {
-                        const float4 p = q[R + k][v], m = q[R - k][v];
-                        s.x = fmaf(a.wz[k], p.x + m.x, s.x);
-                        s.y = fmaf(a.wz[k], p.y + m.y, s.y);
-                        s.z = fmaf(a.wz[k], p.z + m.z, s.z);
-                        s.w = fmaf(a.wz[k], p.w + m.w, s.w);
-                    }
-                    float xs[2 * C::RA + 4];
-                    const float *row = Cp + (rbase + v) * C::PW + 4 * tx;
-#pragma unroll
-                    for (int t = 0; t < (2 * C::RA + 4) / 4; ++t) {
-                        const float4 f = *reinterpret_cast<const float4 *>(row + 4 * t);
-                        xs[4 * t + 0] = f.x;
-                        xs[4 * t + 1] = f.y;
-                        xs[4 * t + 2] = f.z;
-                        xs[4 * t + 3] = f.w;
-                    }
-#pragma unroll
-                    for (int k = 1; k <= R; ++k) {
-                        s.x = fmaf(a.wx[k], xs[C::RA + 0 + k] + xs[C::RA + 0 - k], s.x);
-                        s.y = fmaf(a.wx[k], xs[C::RA + 1 + k] + xs[C::RA + 1 - k], s.y);
-                        s.z = fmaf(a.wx[k], xs[C::RA + 2 + k] + xs[C::RA + 2 - k], s.z);
-                        s.w = fmaf(a.wx[k], xs[C::RA + 3 + k] + xs[C::RA + 3 - k], s.w);
-                    }
-                    acc[v] = s;
-                }
-                // y-neighbours: stream the rows once, each feeds every output row
-                // of this thread within reach.
-#pragma unroll
-                for (int dy = -R; dy < VY + R; ++dy) {
-                    bool needed = false;
-#pragma unroll
-                    for (int v = 0; v < VY; ++v) {
-                        const int k = dy > v ? dy - v : v - dy;
-                        if (k >= 1 && k <= R) needed = true;
-                    }
-                    if (!needed) continue;
-                    const float4 f = *reinterpret_cast<const float4 *>(
-                        Cp + (rbase + dy) * C::PW + C::RA + 4 * tx);
-#pragma unroll
-                    for (int v = 0; v < VY; ++v) {
-                        const int k = dy > v ? dy - v : v - dy;
-                        if (k >= 1 && k <= R) {
-                            acc[v].x = fmaf(a.wy[k], f.x, acc[v].x);
-                            acc[v].y = fmaf(a.wy[k], f.y, acc[v].y);
-                            acc[v].z = fmaf(a.wy[k], f.z, acc[v].z);
-                            acc[v].w = fmaf(a.wy[k], f.w, acc[v].w);
-                        }
-                    }
-                }
-                const float dz = a.dpz[zo];
-#pragma unroll
-                for (int v = 0; v < VY; ++v) {
-                    if (!(xok && yok[v])) continue;
-                    const float4 c = q[R][v];
-                    const float4 b = bb[v], p = um[v], s = acc[v];
-                    const float dyz = dpyv[v] + dz;
-                    float4 o;
-                    o.x = c.x + (1.f - (dpx4[0] + dyz) * b.x) * (c.x - p.x) + b.x * s.x;
-                    o.y = c.y + (1.f - (dpx4[1] + dyz) * b.y) * (c.y - p.y) + b.y * s.y;
-                    o.z = c.z + (1.f - (dpx4[2] + dyz) * b.z) * (c.z - p.z) + b.z * s.z;
-                    o.w = c.w + (1.f - (dpx4[3] + dyz) * b.w) * (c.w - p.w) + b.w * s.w;
-                    const int64_t off = (int64_t)zo * a.L.plane + (int64_t)gy[v] * a.L.nxp + gx;
-                    *reinterpret_cast<float4 *>(unew + off) = o;
+            for (int i = 0; i < 2 * R; ++i) {
+                if (i == R) {
+                    acc[i][v].x += lxy[v].x;
+                    acc[i][v].y += lxy[v].y;
+                    acc[i][v].z += lxy[v].z;
+                    acc[i][v].w += lxy[v].w;
+                } else {
+                    const float w = a.wz[i < R ? R - i : i - R];
+                    acc[i][v].x = fmaf(w, c.x, acc[i][v].x);
+                    acc[i][v].y = fmaf(w, c.y, acc[i][v].y);
+                    acc[i][v].z = fmaf(w, c.z, acc[i][v].z);
+                    acc[i][v].w = fmaf(w, c.w, acc[i][v].w);
                 }
             }
         }
-        __syncthreads();
-        if (s_abort) break;
+
+        // output plane zo = p - R is complete
+        if (j >= 2 * R) {
+            const int zo = za - 2 * R + j;
+            const float dz = a.dpz[zo];
+            const float *Ui = H + C::HALO;
+            const float *Pi = Ui + C::INT;
+            const float *Bi = Pi + C::INT;
+#pragma unroll
+            for (int v = 0; v < VY; ++v) {
+                if (!(xok && yok[v])) continue;
+                const int q = (ty * VY + v) * C::BX + 4 * tx;
+                const float4 c = *reinterpret_cast<const float4 *>(Ui + q);
+                const float4 p = *reinterpret_cast<const float4 *>(Pi + q);
+                const float4 b = *reinterpret_cast<const float4 *>(Bi + q);
+                const float4 s = acc[0][v];
+                const float dyz = dpyv[v] + dz;
+                float4 o;
+                o.x = c.x + (1.f - (dpx4[0] + dyz) * b.x) * (c.x - p.x) + b.x * s.x;
+                o.y = c.y + (1.f - (dpx4[1] + dyz) * b.y) * (c.y - p.y) + b.y * s.y;
+                o.z = c.z + (1.f - (dpx4[2] + dyz) * b.z) * (c.z - p.z) + b.z * s.z;
+                o.w = c.w + (1.f - (dpx4[3] + dyz) * b.w) * (c.w - p.w) + b.w * s.w;
+                const int64_t off = (int64_t)zo * a.L.plane + (int64_t)gy[v] * a.L.nxp + gx;
+                *reinterpret_cast<float4 *>(unew + off) = o;
+            }
+        }
+        // every thread is done with the stage: release it
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+
+        // rotate the pending outputs; plane p + R starts with w_R u(p)
+#pragma unroll
+        for (int v = 0; v < VY; ++v) {
+#pragma unroll
+            for (int i = 0; i < 2 * R - 1; ++i) acc[i][v] = acc[i + 1][v];
+            const float4 c = cen[v];
+            acc[2 * R - 1][v] =
+                make_float4(a.wz[R] * c.x, a.wz[R] * c.y, a.wz[R] * c.z, a.wz[R] * c.w);
+        }
     }
-    if (s_abort && tid == 0) {
-        // Planes 0 .. j+D have been issued; give the ones not yet consumed a
-        // bounded chance to land before the CTA's shared memory goes away.
-        const int issued = min(nplanes, j + D + 1);
-        for (int jj = j; jj < issued; ++jj)
-            mbar_wait_bounded(&bars[jj % C::NS], (uint32_t)((jj / C::NS) & 1), 200000000ull);
+    __syncthreads();
+    if (*abort_flag && tid == 0) {
+        // The last NSL issued stages may still be in flight: give them a
+        // bounded chance to land before the CTA's shared memory is released.
+        for (int jj = issued - C::NSL; jj < issued; ++jj)
+            if (jj >= 0)
+                mbar_wait_bounded(&full[jj % C::NSL], (uint32_t)((jj / C::NSL) & 1), 200000000ull);
     }
 }
 
@@ -242,22 +292,23 @@ struct ConfigEntry {
 template <int R, int TX, int TY, int VY, int D>
 ConfigEntry make_entry(const char *name) {
     using C = AcCfg<R, TX, TY, VY, D>;
-    return ConfigEntry{R,      TX,     TY,     VY,         D,    (const void *)&acoustic_step_kernel<R, TX, TY, VY, D>,
+    return ConfigEntry{R,       TX,    TY,    VY,    D,         (const void *)&acoustic_step_kernel<R, TX, TY, VY, D>,
                        C::SMEM, C::BX, C::BY, C::PW, C::PH, C::THREADS, name};
 }
 
-#define FD_AC_ENTRY(R, TX, TY, VY, D) make_entry<R, TX, TY, VY, D>("acoustic_step<" #R "," #TX "," #TY "," #VY "," #D ">")
+#define FD_AC_ENTRY(R, TX, TY, VY, D) \
+    make_entry<R, TX, TY, VY, D>("acoustic_step<" #R "," #TX "," #TY "," #VY "," #D ">")
 
 const ConfigEntry *config_table(int radius, int *count) {
     static const ConfigEntry r1[] = {FD_AC_ENTRY(1, 16, 8, 2, 3)};
-    static const ConfigEntry r2[] = {FD_AC_ENTRY(2, 16, 8, 2, 3), FD_AC_ENTRY(2, 16, 8, 4, 3),
-                                     FD_AC_ENTRY(2, 32, 4, 2, 3)};
-    static const ConfigEntry r4[] = {FD_AC_ENTRY(4, 16, 8, 2, 2), FD_AC_ENTRY(4, 16, 8, 4, 2),
-                                     FD_AC_ENTRY(4, 32, 4, 2, 2)};
-    static const ConfigEntry r6[] = {FD_AC_ENTRY(6, 16, 8, 2, 2), FD_AC_ENTRY(6, 16, 4, 2, 2),
-                                     FD_AC_ENTRY(6, 32, 4, 2, 2)};
-    static const ConfigEntry r8[] = {FD_AC_ENTRY(8, 16, 8, 1, 2), FD_AC_ENTRY(8, 16, 4, 2, 2),
-                                     FD_AC_ENTRY(8, 16, 8, 2, 2)};
+    static const ConfigEntry r2[] = {FD_AC_ENTRY(2, 16, 8, 2, 3), FD_AC_ENTRY(2, 16, 4, 4, 3),
+                                     FD_AC_ENTRY(2, 16, 16, 1, 3)};
+    static const ConfigEntry r4[] = {FD_AC_ENTRY(4, 16, 8, 2, 2), FD_AC_ENTRY(4, 16, 4, 4, 2),
+                                     FD_AC_ENTRY(4, 16, 16, 1, 2)};
+    static const ConfigEntry r6[] = {FD_AC_ENTRY(6, 16, 8, 2, 2), FD_AC_ENTRY(6, 16, 16, 1, 2),
+                                     FD_AC_ENTRY(6, 16, 8, 1, 2)};
+    static const ConfigEntry r8[] = {FD_AC_ENTRY(8, 16, 8, 2, 2), FD_AC_ENTRY(8, 16, 16, 1, 2),
+                                     FD_AC_ENTRY(8, 16, 8, 1, 2)};
     switch (radius) {
         case 1: *count = 1; return r1;
         case 2: *count = 3; return r2;
@@ -282,7 +333,7 @@ int acoustic_default_config(int radius) {
 }
 
 fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots, float *wave,
-                        AcousticPlan *plan) {
+                        const float *bcoef, AcousticPlan *plan) {
     int n = 0;
     const ConfigEntry *tab = config_table(radius, &n);
     if (!tab) return set_error(FD_ERR_SO, "no acoustic kernel for radius %d", radius);
@@ -320,9 +371,14 @@ fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots,
     plan->grid = dim3(ntx, nty, nshots * nzc);
     plan->zchunk = zchunk;
     plan->nzc = nzc;
-    return make_tensor_map_4d(&plan->map, wave, L.nx, L.ny, L.nz, 2ull * nshots,
+    FD_TRY(make_tensor_map_4d(&plan->map_halo, wave, L.nx, L.ny, L.nz, 2ull * nshots,
                               (uint64_t)L.nxp * 4, (uint64_t)L.plane * 4, (uint64_t)L.vol * 4,
-                              e.pw, e.ph, 1, 1);
+                              e.pw, e.ph, 1, 1));
+    FD_TRY(make_tensor_map_4d(&plan->map_int, wave, L.nx, L.ny, L.nz, 2ull * nshots,
+                              (uint64_t)L.nxp * 4, (uint64_t)L.plane * 4, (uint64_t)L.vol * 4,
+                              e.bx, e.by, 1, 1));
+    return make_tensor_map_4d(&plan->map_b, bcoef, L.nx, L.ny, L.nz, 1, (uint64_t)L.nxp * 4,
+                              (uint64_t)L.plane * 4, (uint64_t)L.vol * 4, e.bx, e.by, 1, 1);
 }
 
 fd_status acoustic_launch(const AcousticPlan &plan, const AcousticStepArgs &args,
@@ -331,7 +387,8 @@ fd_status acoustic_launch(const AcousticPlan &plan, const AcousticStepArgs &args
     const ConfigEntry *tab = config_table(plan.radius, &n);
     if (!tab || plan.config >= n) return set_error(FD_ERR_SO, "bad acoustic plan");
     int zchunk = plan.zchunk, nzc = plan.nzc;
-    void *params[] = {(void *)&plan.map, (void *)&args, (void *)&zchunk, (void *)&nzc};
+    void *params[] = {(void *)&plan.map_halo, (void *)&plan.map_int, (void *)&plan.map_b,
+                      (void *)&args, (void *)&zchunk, (void *)&nzc};
     FD_CUDA_TRY(cudaLaunchKernel(tab[plan.config].fn, plan.grid, plan.block, params, plan.smem,
                                  stream));
     note_launch(stream);

@@ -347,7 +347,7 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     // ---- K1 plan and arguments
     AcousticPlan plan;
     FD_STAGE(s, "acoustic: initial state");
-    FD_TRY(acoustic_plan(R, g_acoustic_config[R], L, nshots, wave, &plan));
+    FD_TRY(acoustic_plan(R, g_acoustic_config[R], L, nshots, wave, bcoef, &plan));
     FD_STAGE(s, plan.name);
     AcousticStepArgs a;
     memset(&a, 0, sizeof(a));

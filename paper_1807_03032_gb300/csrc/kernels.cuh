@@ -49,7 +49,9 @@ struct AcousticStepArgs {
 struct AcousticPlan {
     int radius = 0;
     int config = 0;
-    CUtensorMap map;      // 4-D map over all wavefield buffers
+    CUtensorMap map_halo;  // wavefield buffers, tile + halo box
+    CUtensorMap map_int;   // wavefield buffers, interior tile box
+    CUtensorMap map_b;     // b coefficient, interior tile box
     dim3 grid, block;
     size_t smem = 0;
     int zchunk = 0, nzc = 1;
@@ -59,7 +61,7 @@ struct AcousticPlan {
 int acoustic_num_configs(int radius);
 int acoustic_default_config(int radius);
 fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots, float *wave,
-                        AcousticPlan *plan);
+                        const float *bcoef, AcousticPlan *plan);
 fd_status acoustic_launch(const AcousticPlan &plan, const AcousticStepArgs &args,
                           cudaStream_t stream);
 
