@@ -130,6 +130,43 @@ fd_status tti_forward(const fd_grid *grid, int so, double dt, int nt, int nshots
                       const float *p_init, const float *r_init, float *p_final, float *r_final,
                       void *stream);
 
+/*
+ * acoustic_forward_noalloc -- acoustic_forward for callers that cannot
+ * allocate device memory.  The paper has no counterpart; this is a library
+ * convenience.
+ *
+ * acoustic_forward allocates its workspace (padded wavefields, the b
+ * coefficient, sparse tables) with cudaMallocAsync on every call.  Some callers
+ * cannot allow that: code running under a fixed device-memory budget decided
+ * up front, a process whose device memory belongs to another allocator (a
+ * framework's caching pool), or a service that must not hit out-of-memory in
+ * the middle of a request.  This entry point computes exactly what
+ * acoustic_forward computes but keeps the workspace in one fixed, file-scope
+ * device array of FD_STATIC_SCRATCH_BYTES, so a call allocates nothing
+ * (no cudaMalloc, cudaFree, stream, event or graph creation).
+ *
+ *  - Arguments, layouts and results are those of acoustic_forward, except
+ *    that every pointer must be device memory (FD_ERR_ARG otherwise) and the
+ *    work runs directly on `stream` (synchronised once at the end).
+ *  - A problem whose workspace, 4 * (2 nshots + 1) * nz * ny * nxp bytes
+ *    (nxp = nx rounded up to a multiple of 4) plus its sparse tables, exceeds
+ *    FD_STATIC_SCRATCH_BYTES is rejected with FD_ERR_ARG before any launch.
+ *  - Every GPU that loads the library holds the array until the process
+ *    exits.  All calls share it and it keeps the last call's contents; each
+ *    call clears what must start at zero.  Calls that overlap on the GPU
+ *    (other streams or host threads on the same device) race on the array and
+ *    must be serialised by the caller.
+ *  - The first call on a device looks up the array's address with
+ *    cudaGetSymbolAddress (that device current) and caches it; make that first
+ *    call before any CUDA stream capture.
+ */
+#define FD_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+fd_status acoustic_forward_noalloc(const fd_grid *grid, int so, double dt, int nt, int nshots,
+                                   const float *m, const float *damp, int nsrc,
+                                   const float *src_xyz, const float *src_wav, int nrec,
+                                   const float *rec_xyz, float *rec_out, const float *u_init,
+                                   float *u_final, void *stream);
+
 /* Message describing the last error on the calling thread ("" if none). */
 const char *fd_last_error(void);
 
