@@ -49,10 +49,63 @@ struct AcCfg {
     static constexpr uint32_t INT_BYTES = INT * 4;
     static constexpr int THREADS = TX * TY;
     static constexpr int WARPS = THREADS / 32;
+    // stages, full/empty mbarriers, abort flag; + damp_z of the z chunk
+    // (added at launch) and 128 bytes to align the base
     static constexpr size_t SMEM = (size_t)NSL * STAGE * 4 + NSL * 16 + 16 + 128;
     static_assert(PW <= 256 && PH <= 256 && BX <= 256 && BY <= 256, "TMA box dimension limit");
     static_assert(INT % 32 == 0 && THREADS % 32 == 0, "tile shape");
 };
+
+// Packed FP32 pairs: Blackwell executes fma/add/sub/mul.rn.f32x2 on a 64-bit
+// register pair as two independently rounded FP32 operations, so results are
+// bit-identical to the scalar forms at half the instruction count.
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float f2_lo(f2 v) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return lo;
+}
+__device__ __forceinline__ float f2_hi(f2 v) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return hi;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_splat(float w) { return f2_pack(w, w); }
+
+// Four consecutive x points as two packed pairs.
+struct Q4 {
+    f2 lo, hi;
+};
+__device__ __forceinline__ Q4 lds_q4(const float *p) {
+    const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(p);
+    return Q4{t.x, t.y};
+}
 
 template <int R, int TX, int TY, int VY, int D>
 __global__ void __launch_bounds__(TX *TY)
@@ -67,6 +120,7 @@ __global__ void __launch_bounds__(TX *TY)
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::NSL * C::STAGE);
     uint64_t *empty = full + C::NSL;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + C::NSL);
+    float *sdz = reinterpret_cast<float *>(empty + C::NSL + 2);  // damp_z / dt of this chunk
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -91,6 +145,7 @@ __global__ void __launch_bounds__(TX *TY)
         fence_mbar_init();
         *abort_flag = 0;
     }
+    for (int z = za + tid; z < zb; z += C::THREADS) sdz[z - za] = a.dpz[z];
     __syncthreads();
 
     // Producer (thread 0): stage for iteration jj = halo plane za-R+jj, plus
@@ -121,6 +176,7 @@ __global__ void __launch_bounds__(TX *TY)
     float dpx4[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) dpx4[i] = (gx + i < a.L.nx) ? a.dpx[gx + i] : 0.f;
+    const f2 dpx_lo = f2_pack(dpx4[0], dpx4[1]), dpx_hi = f2_pack(dpx4[2], dpx4[3]);
     int gy[VY];
     bool yok[VY];
     float dpyv[VY];
@@ -131,13 +187,14 @@ __global__ void __launch_bounds__(TX *TY)
         dpyv[v] = yok[v] ? a.dpy[gy[v]] : 0.f;
     }
     float *__restrict__ unew = a.wave + (int64_t)wprev * a.L.vol;
+    const f2 one2 = f2_splat(1.f);
 
     // acc[i][v]: pending output plane p - R + i (p = arriving plane)
-    float4 acc[2 * R][VY];
+    Q4 acc[2 * R][VY];
 #pragma unroll
     for (int i = 0; i < 2 * R; ++i)
 #pragma unroll
-        for (int v = 0; v < VY; ++v) acc[i][v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int v = 0; v < VY; ++v) acc[i][v] = Q4{0ull, 0ull};
 
     bool failed = false;
     for (int j = 0; j < nplanes; ++j) {
@@ -159,32 +216,44 @@ __global__ void __launch_bounds__(TX *TY)
 
         // x/y part of the Laplacian of plane p (centre weight of all axes
         // included) and the centre values
-        float4 cen[VY], lxy[VY];
+        Q4 cen[VY], lxy[VY];
 #pragma unroll
         for (int v = 0; v < VY; ++v) {
-            float xs[2 * C::RA + 4];
+            constexpr int NP = (2 * C::RA + 4) / 2;  // packed pairs in the x span
+            f2 xp[NP];
             const float *row = H + (rbase + v) * C::PW + 4 * tx;
 #pragma unroll
-            for (int t = 0; t < (2 * C::RA + 4) / 4; ++t) {
-                const float4 f = *reinterpret_cast<const float4 *>(row + 4 * t);
-                xs[4 * t + 0] = f.x;
-                xs[4 * t + 1] = f.y;
-                xs[4 * t + 2] = f.z;
-                xs[4 * t + 3] = f.w;
+            for (int t = 0; t < NP / 2; ++t) {
+                const Q4 q = lds_q4(row + 4 * t);
+                xp[2 * t] = q.lo;
+                xp[2 * t + 1] = q.hi;
             }
-            const float4 c = make_float4(xs[C::RA], xs[C::RA + 1], xs[C::RA + 2], xs[C::RA + 3]);
-            float4 s;
-            s.x = a.wc * c.x;
-            s.y = a.wc * c.y;
-            s.z = a.wc * c.z;
-            s.w = a.wc * c.w;
+            constexpr int c0 = C::RA / 2;  // pair index of points 0,1
+            const Q4 c = Q4{xp[c0], xp[c0 + 1]};
+            const f2 wc2 = f2_splat(a.wc);
+            Q4 s = Q4{f2_mul(wc2, c.lo), f2_mul(wc2, c.hi)};
+            // even shifts keep the pair alignment: packed arithmetic
 #pragma unroll
-            for (int k = 1; k <= R; ++k) {
-                s.x = fmaf(a.wx[k], xs[C::RA + 0 + k] + xs[C::RA + 0 - k], s.x);
-                s.y = fmaf(a.wx[k], xs[C::RA + 1 + k] + xs[C::RA + 1 - k], s.y);
-                s.z = fmaf(a.wx[k], xs[C::RA + 2 + k] + xs[C::RA + 2 - k], s.z);
-                s.w = fmaf(a.wx[k], xs[C::RA + 3 + k] + xs[C::RA + 3 - k], s.w);
+            for (int k = 2; k <= R; k += 2) {
+                const f2 w2 = f2_splat(a.wx[k]);
+                s.lo = f2_fma(w2, f2_add(xp[c0 + k / 2], xp[c0 - k / 2]), s.lo);
+                s.hi = f2_fma(w2, f2_add(xp[c0 + 1 + k / 2], xp[c0 + 1 - k / 2]), s.hi);
             }
+            // odd shifts straddle the pairs: scalar arithmetic
+            float o0 = 0.f, o1 = 0.f, o2 = 0.f, o3 = 0.f;
+#pragma unroll
+            for (int k = 1; k <= R; k += 2) {
+                auto el = [&](int idx) -> float {
+                    return (idx & 1) ? f2_hi(xp[idx >> 1]) : f2_lo(xp[idx >> 1]);
+                };
+                const float w = a.wx[k];
+                o0 = fmaf(w, el(C::RA + 0 + k) + el(C::RA + 0 - k), o0);
+                o1 = fmaf(w, el(C::RA + 1 + k) + el(C::RA + 1 - k), o1);
+                o2 = fmaf(w, el(C::RA + 2 + k) + el(C::RA + 2 - k), o2);
+                o3 = fmaf(w, el(C::RA + 3 + k) + el(C::RA + 3 - k), o3);
+            }
+            s.lo = f2_add(s.lo, f2_pack(o0, o1));
+            s.hi = f2_add(s.hi, f2_pack(o2, o3));
             cen[v] = c;
             lxy[v] = s;
         }
@@ -197,16 +266,14 @@ __global__ void __launch_bounds__(TX *TY)
                 if (k >= 1 && k <= R) needed = true;
             }
             if (!needed) continue;
-            const float4 f =
-                *reinterpret_cast<const float4 *>(H + (rbase + dy) * C::PW + C::RA + 4 * tx);
+            const Q4 f = lds_q4(H + (rbase + dy) * C::PW + C::RA + 4 * tx);
 #pragma unroll
             for (int v = 0; v < VY; ++v) {
                 const int k = dy > v ? dy - v : v - dy;
                 if (k >= 1 && k <= R) {
-                    lxy[v].x = fmaf(a.wy[k], f.x, lxy[v].x);
-                    lxy[v].y = fmaf(a.wy[k], f.y, lxy[v].y);
-                    lxy[v].z = fmaf(a.wy[k], f.z, lxy[v].z);
-                    lxy[v].w = fmaf(a.wy[k], f.w, lxy[v].w);
+                    const f2 w2 = f2_splat(a.wy[k]);
+                    lxy[v].lo = f2_fma(w2, f.lo, lxy[v].lo);
+                    lxy[v].hi = f2_fma(w2, f.hi, lxy[v].hi);
                 }
             }
         }
@@ -214,28 +281,25 @@ __global__ void __launch_bounds__(TX *TY)
         // z part: plane p feeds the pending outputs p-R .. p+R-1 and starts p+R
 #pragma unroll
         for (int v = 0; v < VY; ++v) {
-            const float4 c = cen[v];
+            const Q4 c = cen[v];
 #pragma unroll
             for (int i = 0; i < 2 * R; ++i) {
                 if (i == R) {
-                    acc[i][v].x += lxy[v].x;
-                    acc[i][v].y += lxy[v].y;
-                    acc[i][v].z += lxy[v].z;
-                    acc[i][v].w += lxy[v].w;
+                    acc[i][v].lo = f2_add(acc[i][v].lo, lxy[v].lo);
+                    acc[i][v].hi = f2_add(acc[i][v].hi, lxy[v].hi);
                 } else {
-                    const float w = a.wz[i < R ? R - i : i - R];
-                    acc[i][v].x = fmaf(w, c.x, acc[i][v].x);
-                    acc[i][v].y = fmaf(w, c.y, acc[i][v].y);
-                    acc[i][v].z = fmaf(w, c.z, acc[i][v].z);
-                    acc[i][v].w = fmaf(w, c.w, acc[i][v].w);
+                    const f2 w2 = f2_splat(a.wz[i < R ? R - i : i - R]);
+                    acc[i][v].lo = f2_fma(w2, c.lo, acc[i][v].lo);
+                    acc[i][v].hi = f2_fma(w2, c.hi, acc[i][v].hi);
                 }
             }
         }
 
-        // output plane zo = p - R is complete
+        // output plane zo = p - R is complete:
+        //   u+ = u + (1 - zeta)(u - u-) + b * acc,  zeta = (dx + dy + dz) b
         if (j >= 2 * R) {
             const int zo = za - 2 * R + j;
-            const float dz = a.dpz[zo];
+            const float dz = sdz[zo - za];
             const float *Ui = H + C::HALO;
             const float *Pi = Ui + C::INT;
             const float *Bi = Pi + C::INT;
@@ -243,18 +307,19 @@ __global__ void __launch_bounds__(TX *TY)
             for (int v = 0; v < VY; ++v) {
                 if (!(xok && yok[v])) continue;
                 const int q = (ty * VY + v) * C::BX + 4 * tx;
-                const float4 c = *reinterpret_cast<const float4 *>(Ui + q);
-                const float4 p = *reinterpret_cast<const float4 *>(Pi + q);
-                const float4 b = *reinterpret_cast<const float4 *>(Bi + q);
-                const float4 s = acc[0][v];
-                const float dyz = dpyv[v] + dz;
-                float4 o;
-                o.x = c.x + (1.f - (dpx4[0] + dyz) * b.x) * (c.x - p.x) + b.x * s.x;
-                o.y = c.y + (1.f - (dpx4[1] + dyz) * b.y) * (c.y - p.y) + b.y * s.y;
-                o.z = c.z + (1.f - (dpx4[2] + dyz) * b.z) * (c.z - p.z) + b.z * s.z;
-                o.w = c.w + (1.f - (dpx4[3] + dyz) * b.w) * (c.w - p.w) + b.w * s.w;
+                const Q4 c = lds_q4(Ui + q);
+                const Q4 p = lds_q4(Pi + q);
+                const Q4 b = lds_q4(Bi + q);
+                const Q4 s = acc[0][v];
+                const f2 dyz = f2_splat(dpyv[v] + dz);
+                const f2 zl = f2_mul(f2_add(dpx_lo, dyz), b.lo);
+                const f2 zh = f2_mul(f2_add(dpx_hi, dyz), b.hi);
+                f2 ol = f2_fma(f2_sub(one2, zl), f2_sub(c.lo, p.lo), c.lo);
+                f2 oh = f2_fma(f2_sub(one2, zh), f2_sub(c.hi, p.hi), c.hi);
+                ol = f2_fma(b.lo, s.lo, ol);
+                oh = f2_fma(b.hi, s.hi, oh);
                 const int64_t off = (int64_t)zo * a.L.plane + (int64_t)gy[v] * a.L.nxp + gx;
-                *reinterpret_cast<float4 *>(unew + off) = o;
+                *reinterpret_cast<ulonglong2 *>(unew + off) = make_ulonglong2(ol, oh);
             }
         }
         // every thread is done with the stage: release it
@@ -262,13 +327,12 @@ __global__ void __launch_bounds__(TX *TY)
         if (lane == 0) mbar_arrive(&empty[slot]);
 
         // rotate the pending outputs; plane p + R starts with w_R u(p)
+        const f2 wR2 = f2_splat(a.wz[R]);
 #pragma unroll
         for (int v = 0; v < VY; ++v) {
 #pragma unroll
             for (int i = 0; i < 2 * R - 1; ++i) acc[i][v] = acc[i + 1][v];
-            const float4 c = cen[v];
-            acc[2 * R - 1][v] =
-                make_float4(a.wz[R] * c.x, a.wz[R] * c.y, a.wz[R] * c.z, a.wz[R] * c.w);
+            acc[2 * R - 1][v] = Q4{f2_mul(wR2, cen[v].lo), f2_mul(wR2, cen[v].hi)};
         }
     }
     __syncthreads();
@@ -302,21 +366,21 @@ ConfigEntry make_entry(const char *name) {
 const ConfigEntry *config_table(int radius, int *count) {
     // Index 0 is the default; the others are kept for tuning sweeps
     // (fd_set_acoustic_config).  Defaults measured on GB300 at 512^3.
-    static const ConfigEntry r1[] = {FD_AC_ENTRY(1, 16, 16, 1, 3)};
-    static const ConfigEntry r2[] = {FD_AC_ENTRY(2, 16, 16, 1, 3), FD_AC_ENTRY(2, 16, 8, 2, 3),
-                                     FD_AC_ENTRY(2, 16, 4, 4, 3)};
-    static const ConfigEntry r4[] = {FD_AC_ENTRY(4, 16, 16, 1, 2), FD_AC_ENTRY(4, 16, 8, 2, 2),
-                                     FD_AC_ENTRY(4, 16, 4, 4, 2)};
-    static const ConfigEntry r6[] = {FD_AC_ENTRY(6, 16, 8, 1, 2), FD_AC_ENTRY(6, 16, 16, 1, 2),
-                                     FD_AC_ENTRY(6, 16, 8, 2, 2)};
-    static const ConfigEntry r8[] = {FD_AC_ENTRY(8, 16, 8, 1, 2), FD_AC_ENTRY(8, 16, 16, 1, 2),
-                                     FD_AC_ENTRY(8, 16, 8, 2, 2)};
+    static const ConfigEntry r1[] = {FD_AC_ENTRY(1, 16, 16, 1, 4)};
+    static const ConfigEntry r2[] = {FD_AC_ENTRY(2, 16, 16, 1, 4), FD_AC_ENTRY(2, 16, 16, 1, 6),
+                                     FD_AC_ENTRY(2, 16, 8, 1, 6), FD_AC_ENTRY(2, 16, 8, 2, 4)};
+    static const ConfigEntry r4[] = {FD_AC_ENTRY(4, 16, 8, 1, 3), FD_AC_ENTRY(4, 16, 8, 1, 5),
+                                     FD_AC_ENTRY(4, 16, 16, 1, 4), FD_AC_ENTRY(4, 16, 8, 2, 3)};
+    static const ConfigEntry r6[] = {FD_AC_ENTRY(6, 16, 8, 1, 2), FD_AC_ENTRY(6, 16, 8, 1, 4),
+                                     FD_AC_ENTRY(6, 16, 16, 1, 3), FD_AC_ENTRY(6, 8, 16, 1, 3)};
+    static const ConfigEntry r8[] = {FD_AC_ENTRY(8, 16, 8, 1, 2), FD_AC_ENTRY(8, 16, 8, 1, 4),
+                                     FD_AC_ENTRY(8, 16, 16, 1, 3), FD_AC_ENTRY(8, 8, 16, 1, 3)};
     switch (radius) {
         case 1: *count = 1; return r1;
-        case 2: *count = 3; return r2;
-        case 4: *count = 3; return r4;
-        case 6: *count = 3; return r6;
-        case 8: *count = 3; return r8;
+        case 2: *count = 4; return r2;
+        case 4: *count = 4; return r4;
+        case 6: *count = 4; return r6;
+        case 8: *count = 4; return r8;
         default: *count = 0; return nullptr;
     }
 }
@@ -373,6 +437,10 @@ fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots,
     plan->grid = dim3(ntx, nty, nshots * nzc);
     plan->zchunk = zchunk;
     plan->nzc = nzc;
+    plan->smem = e.smem + (size_t)zchunk * 4;
+    if (plan->smem > e.smem)
+        FD_CUDA_TRY(cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)plan->smem));
     FD_TRY(make_tensor_map_4d(&plan->map_halo, wave, L.nx, L.ny, L.nz, 2ull * nshots,
                               (uint64_t)L.nxp * 4, (uint64_t)L.plane * 4, (uint64_t)L.vol * 4,
                               e.pw, e.ph, 1, 1));
