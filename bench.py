@@ -143,11 +143,35 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def shard_shots(nshots_total, rank, world):
+    """Contiguous block of global shot indices owned by `rank` (shots are
+    independent problems: no data moves between ranks)."""
+    base, extra = divmod(nshots_total, world)
+    start = rank * base + min(rank, extra)
+    return range(start, start + base + (1 if rank < extra else 0))
+
+
+def max_over_ranks(value, world, device=None):
+    """Maximum of a per-rank float over all ranks (the job's elapsed time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shot_source_offset(shot, spacing):
+    """Global shot `shot` fires at the workload's source shifted 7 cells in x
+    per shot index."""
+    return np.float32(shot * 7 * spacing)
+
+
 def build_workload(rank, n, so):
     w = workloads.acoustic_large(n=n, so=so, nt=None)
-    if rank:
-        # each rank models its own shot: shift the source along x
-        w.src_xyz[..., 0] += np.float32(rank * 7 * w.spacing[0])
+    shots = shard_shots(dist_env()[0], rank, dist_env()[0])
+    w.src_xyz[..., 0] += shot_source_offset(shots[0], w.spacing[0])
     return w
 
 
@@ -221,12 +245,7 @@ def run_ours(args):
     k1_ms, k1_n, k1_pts = _native.stats_get("acoustic_step")
     sp_ms, sp_n, _ = _native.stats_get("sparse")
     _native.stats_enable(False)
-    elapsed_ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), ws, dev)
     total_points = points_per_forward * len(args.so) * args.steps * ws
     value = total_points / (elapsed_ms * 1e-3) / 1e9
     ms_per_step = elapsed_ms / args.steps
@@ -290,12 +309,7 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        e_ms = e0.elapsed_time(e1)
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
+        e_ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
         e2e = {"value": round(points_per_forward * len(args.so) * ksteps * ws / (e_ms * 1e-3) / 1e9, 2),
                "unit": "GPts/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "steps": ksteps, "host_memory": "pinned"}
