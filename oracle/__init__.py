@@ -88,7 +88,10 @@ def _load():
             lib.ora_tti_operators.argtypes = [G, I, I, P, P, P, P, P]
             lib.ora_tti_forward.argtypes = [G, I, I, D, I, I, P, P, P, P, P, P,
                                             I, P, P, I, P, P, P, P, P, P]
-            for name in ("ora_laplacian", "ora_first_derivative", "ora_acoustic_step",
+            lib.ora_acoustic_adjoint.argtypes = [G, I, I, D, I, I, P, P, I, P, P, I, P, P]
+            lib.ora_acoustic_gradient.argtypes = [G, I, D, I, I, P, P, I, P, P, I, P, P, P]
+            for name in ("ora_acoustic_adjoint", "ora_acoustic_gradient",
+                         "ora_laplacian", "ora_first_derivative", "ora_acoustic_step",
                          "ora_interpolate", "ora_inject", "ora_acoustic_forward",
                          "ora_tti_operators", "ora_tti_forward"):
                 getattr(lib, name).restype = ctypes.c_int
@@ -228,3 +231,41 @@ def tti_forward(grid: Grid, so: int, dt: float, nt: int, m, eps, delta, theta, p
                                  _ptr(pfin), _ptr(rfin))
     _check(st, "tti_forward")
     return rec, pfin, rfin
+
+
+def acoustic_adjoint(grid: Grid, so: int, dt: float, nt: int, m, src_xyz, rec_xyz, rec_resid,
+                     damp=None, periodic: bool = False):
+    """Adjoint of the source-to-receiver map of `acoustic_forward` (zero initial
+    state): receiver residuals [nshots][nt][nrec] -> source-wavelet gradient
+    [nshots][nt][nsrc] (FP64)."""
+    m = _f32(m)
+    damp = _f32(damp)
+    src_xyz, rec_xyz = _f32(src_xyz), _f32(rec_xyz)
+    rr = _f64(rec_resid)
+    nshots, nsrc = src_xyz.shape[0], src_xyz.shape[1]
+    nrec = rec_xyz.shape[1]
+    out = np.zeros((nshots, nt, nsrc))
+    st = _load().ora_acoustic_adjoint(ctypes.byref(grid), so, int(periodic), float(dt), int(nt),
+                                      nshots, _ptr(m), _ptr(damp), nsrc, _ptr(src_xyz), _ptr(out),
+                                      nrec, _ptr(rec_xyz), _ptr(rr))
+    _check(st, "acoustic_adjoint")
+    return out
+
+
+def acoustic_gradient(grid: Grid, so: int, dt: float, nt: int, m, src_xyz, src_wav, rec_xyz,
+                      rec_resid, damp=None):
+    """Gradient with respect to m of <rec_resid, d(m)> summed over shots
+    ([nz][ny][nx], FP64); with rec_resid = d(m) - d_obs it is the gradient of
+    J(m) = 1/2 ||d(m) - d_obs||^2."""
+    m = _f32(m)
+    damp = _f32(damp)
+    src_xyz, src_wav, rec_xyz = _f32(src_xyz), _f32(src_wav), _f32(rec_xyz)
+    rr = _f64(rec_resid)
+    nshots, nsrc = src_xyz.shape[0], src_xyz.shape[1]
+    nrec = rec_xyz.shape[1]
+    grad = np.zeros(m.shape)
+    st = _load().ora_acoustic_gradient(ctypes.byref(grid), so, float(dt), int(nt), nshots,
+                                       _ptr(m), _ptr(damp), nsrc, _ptr(src_xyz), _ptr(src_wav),
+                                       nrec, _ptr(rec_xyz), _ptr(rr), _ptr(grad))
+    _check(st, "acoustic_gradient")
+    return grad

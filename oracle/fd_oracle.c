@@ -496,3 +496,203 @@ done:
     for (int b = 0; b < 10; ++b) free(bufs[b]);
     return st;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint and gradient (the adjoint-state method the paper names as the
+ * purpose of time-subsampled saving: "data inversion using adjoint-state
+ * methods").  The paper prints no adjoint; what follows is the exact transpose
+ * of the discrete forward map above, derived from it:
+ *
+ *   forward   u^{n+1} = M1 u^n - M2 u^{n-1} + B S^T q^n,  d^n = R u^n,
+ *             M1 = 2 - zeta + B L,  M2 = 1 - zeta,  B = dt^2/(m + eta),
+ *             zeta = damp dt/(m + eta)   (all diagonal except L),
+ *   adjoint   lambda^n = R^T dd^n + M1^T lambda^{n+1} - M2^T lambda^{n+2},
+ *             M1^T x = (2 - zeta) x + L (B x),  M2^T x = (1 - zeta) x,
+ *             lambda^{nt} = lambda^{nt+1} = 0,
+ *             dq^n = S B lambda^{n+1}  (n <= nt-2),  dq^{nt-1} = 0,
+ *   gradient  of <dd, d(m)> with respect to m:
+ *             sum_{n=0}^{nt-2} lambda^{n+1} * du^{n+1}/dm,
+ *             du^{n+1}/dm = -(u^{n+1} - 2u^n + u^{n-1}) / (m + eta).
+ * S = source interpolation, R = receiver interpolation (trilinear, Eq. interp).
+ */
+
+/* lam_n = rtd + (2 - zeta) lam1 + L(B lam1) - (1 - zeta) lam2 */
+static int adjoint_step(const ora_grid *g, int so, int periodic, double dt, const double *m,
+                        const double *damp, const double *lam1, const double *lam2,
+                        double *lam_n, double *tmp, double *ltmp) {
+    const size_t N = npts(g);
+    for (int k = 0; k < g->nz; ++k)
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i) {
+                size_t p = lin(g, i, j, k);
+                double eta = damp_at(g, damp, i, j, k) * dt * 0.5;
+                tmp[p] = dt * dt / (m[p] + eta) * lam1[p];
+            }
+    int st = ora_laplacian(g, so, periodic, tmp, ltmp);
+    if (st) return st;
+    for (int k = 0; k < g->nz; ++k)
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i) {
+                size_t p = lin(g, i, j, k);
+                double eta = damp_at(g, damp, i, j, k) * dt * 0.5;
+                double zeta = 2.0 * eta / (m[p] + eta);
+                lam_n[p] = (2.0 - zeta) * lam1[p] + ltmp[p] - (1.0 - zeta) * lam2[p];
+            }
+    (void)N;
+    return ORA_OK;
+}
+
+/* Adjoint of ora_acoustic_forward's source-to-receiver map (zero initial
+ * state).  rec_resid [nshots][nt][nrec] in; src_grad [nshots][nt][nsrc] out. */
+int ora_acoustic_adjoint(const ora_grid *g, int so, int periodic, double dt, int nt, int nshots,
+                         const float *m32, const float *damp32, int nsrc, const float *src_xyz,
+                         double *src_grad, int nrec, const float *rec_xyz,
+                         const double *rec_resid) {
+    if (radius_of(so) < 0 || nt < 1 || nshots < 1 || nsrc < 0 || nrec < 0) return ORA_ERR_ARG;
+    const size_t N = npts(g);
+    for (int s = 0; s < nshots; ++s) {
+        if (check_sparse(g, nsrc, src_xyz + (size_t)s * nsrc * 3)) return ORA_ERR_COORD;
+        if (check_sparse(g, nrec, rec_xyz + (size_t)s * nrec * 3)) return ORA_ERR_COORD;
+    }
+    int st = ORA_OK;
+    double *m = widen(m32, N);
+    double *damp = damp32 ? widen(damp32, (size_t)g->nx + g->ny + g->nz) : NULL;
+    double *l0 = (double *)calloc(N, sizeof(double)), *l1 = (double *)calloc(N, sizeof(double));
+    double *l2 = (double *)calloc(N, sizeof(double)), *tmp = (double *)malloc(N * sizeof(double));
+    double *ltmp = (double *)malloc(N * sizeof(double)), *ones = (double *)malloc(N * sizeof(double));
+    double *bl = (double *)malloc(N * sizeof(double));
+    if (!m || (damp32 && !damp) || !l0 || !l1 || !l2 || !tmp || !ltmp || !ones || !bl) {
+        st = ORA_ERR_OOM;
+        goto done;
+    }
+    for (size_t p = 0; p < N; ++p) ones[p] = 1.0;
+    for (int s = 0; s < nshots; ++s) {
+        const float *sxyz = src_xyz + (size_t)s * nsrc * 3;
+        const float *rxyz = rec_xyz + (size_t)s * nrec * 3;
+        const double *dd = rec_resid + (size_t)s * nt * nrec;
+        double *dq = src_grad + (size_t)s * nt * nsrc;
+        memset(l1, 0, N * sizeof(double)); /* lambda^{n+1} */
+        memset(l2, 0, N * sizeof(double)); /* lambda^{n+2} */
+        for (int n = nt - 1; n >= 0; --n) {
+            /* dq^n = S B lambda^{n+1} */
+            if (nsrc > 0) {
+                if (n <= nt - 2) {
+                    for (int k = 0; k < g->nz; ++k)
+                        for (int j = 0; j < g->ny; ++j)
+                            for (int i = 0; i < g->nx; ++i) {
+                                size_t p = lin(g, i, j, k);
+                                double eta = damp_at(g, damp, i, j, k) * dt * 0.5;
+                                bl[p] = dt * dt / (m[p] + eta) * l1[p];
+                            }
+                    ora_interpolate(g, nsrc, sxyz, bl, dq + (size_t)n * nsrc);
+                } else {
+                    for (int k = 0; k < nsrc; ++k) dq[(size_t)n * nsrc + k] = 0.0;
+                }
+            }
+            st = adjoint_step(g, so, periodic, dt, m, damp, l1, l2, l0, tmp, ltmp);
+            if (st) goto done;
+            /* + R^T dd^n */
+            st = ora_inject(g, nrec, rxyz, dd + (size_t)n * nrec, ones, l0);
+            if (st) goto done;
+            double *t = l2;
+            l2 = l1;
+            l1 = l0;
+            l0 = t;
+        }
+    }
+done:
+    free(m);
+    free(damp);
+    free(l0);
+    free(l1);
+    free(l2);
+    free(tmp);
+    free(ltmp);
+    free(ones);
+    free(bl);
+    return st;
+}
+
+/* Gradient with respect to m of <rec_resid, d(m)> (the FWI gradient when
+ * rec_resid = d(m) - d_obs), zero initial state, summed over shots; keeps the
+ * whole forward history in memory (small grids only).  grad [nz][ny][nx]. */
+int ora_acoustic_gradient(const ora_grid *g, int so, double dt, int nt, int nshots,
+                          const float *m32, const float *damp32, int nsrc, const float *src_xyz,
+                          const float *src_wav, int nrec, const float *rec_xyz,
+                          const double *rec_resid, double *grad) {
+    if (radius_of(so) < 0 || nt < 1 || nshots < 1 || nsrc < 0 || nrec < 0) return ORA_ERR_ARG;
+    const size_t N = npts(g);
+    for (int s = 0; s < nshots; ++s) {
+        if (check_sparse(g, nsrc, src_xyz + (size_t)s * nsrc * 3)) return ORA_ERR_COORD;
+        if (check_sparse(g, nrec, rec_xyz + (size_t)s * nrec * 3)) return ORA_ERR_COORD;
+    }
+    int st = ORA_OK;
+    double *m = widen(m32, N);
+    double *damp = damp32 ? widen(damp32, (size_t)g->nx + g->ny + g->nz) : NULL;
+    double *hist = (double *)malloc((size_t)(nt + 1) * N * sizeof(double)); /* u^{-1..nt-1} */
+    double *scale = (double *)malloc(N * sizeof(double));
+    double *q = (double *)malloc(((size_t)nsrc + 1) * sizeof(double));
+    double *l0 = (double *)calloc(N, sizeof(double)), *l1 = (double *)calloc(N, sizeof(double));
+    double *l2 = (double *)calloc(N, sizeof(double)), *tmp = (double *)malloc(N * sizeof(double));
+    double *ltmp = (double *)malloc(N * sizeof(double)), *ones = (double *)malloc(N * sizeof(double));
+    if (!m || (damp32 && !damp) || !hist || !scale || !q || !l0 || !l1 || !l2 || !tmp || !ltmp ||
+        !ones) {
+        st = ORA_ERR_OOM;
+        goto done;
+    }
+    for (size_t p = 0; p < N; ++p) {
+        ones[p] = 1.0;
+        grad[p] = 0.0;
+    }
+    injection_scale(g, dt, m, damp, scale);
+    for (int s = 0; s < nshots; ++s) {
+        const float *sxyz = src_xyz + (size_t)s * nsrc * 3;
+        const float *rxyz = rec_xyz + (size_t)s * nrec * 3;
+        const double *dd = rec_resid + (size_t)s * nt * nrec;
+#define U(n) (hist + (size_t)((n) + 1) * N)
+        memset(U(-1), 0, N * sizeof(double));
+        memset(U(0), 0, N * sizeof(double));
+        for (int n = 0; n + 1 < nt; ++n) {
+            st = ora_acoustic_step(g, so, 0, dt, m, damp, U(n), U(n - 1), U(n + 1));
+            if (st) goto done;
+            for (int k = 0; k < nsrc; ++k) q[k] = (double)src_wav[((size_t)s * nt + n) * nsrc + k];
+            ora_inject(g, nsrc, sxyz, q, scale, U(n + 1));
+        }
+        memset(l1, 0, N * sizeof(double));
+        memset(l2, 0, N * sizeof(double));
+        for (int n = nt - 1; n >= 0; --n) {
+            /* gradient term of step n -> n+1 uses lambda^{n+1} */
+            if (n <= nt - 2)
+                for (int k = 0; k < g->nz; ++k)
+                    for (int j = 0; j < g->ny; ++j)
+                        for (int i = 0; i < g->nx; ++i) {
+                            size_t p = lin(g, i, j, k);
+                            double eta = damp_at(g, damp, i, j, k) * dt * 0.5;
+                            double du = -(U(n + 1)[p] - 2.0 * U(n)[p] + U(n - 1)[p]) / (m[p] + eta);
+                            grad[p] += l1[p] * du;
+                        }
+            st = adjoint_step(g, so, 0, dt, m, damp, l1, l2, l0, tmp, ltmp);
+            if (st) goto done;
+            st = ora_inject(g, nrec, rxyz, dd + (size_t)n * nrec, ones, l0);
+            if (st) goto done;
+            double *t = l2;
+            l2 = l1;
+            l1 = l0;
+            l0 = t;
+        }
+#undef U
+    }
+done:
+    free(m);
+    free(damp);
+    free(hist);
+    free(scale);
+    free(q);
+    free(l0);
+    free(l1);
+    free(l2);
+    free(tmp);
+    free(ltmp);
+    free(ones);
+    return st;
+}
