@@ -131,6 +131,51 @@ fd_status tti_forward(const fd_grid *grid, int so, double dt, int nt, int nshots
                       void *stream);
 
 /*
+ * acoustic_adjoint -- adjoint of acoustic_forward's source-to-receiver map.
+ *
+ * The paper motivates saving the forward wavefield with "data inversion using
+ * adjoint-state methods" (section "Control flow") but prints no adjoint; this
+ * is the exact transpose of the discrete forward map of acoustic_forward
+ * (zero initial state), so that <F q, d> = <q, F^T d> holds to rounding:
+ *   lambda^n = R^T d^n + M1^T lambda^{n+1} - M2^T lambda^{n+2},
+ *   q_adj^n = S B lambda^{n+1} (n <= nt-2),  q_adj^{nt-1} = 0,
+ * with M1 = 2 - zeta + B L, M2 = 1 - zeta, B = dt^2/(m + damp dt/2), R the
+ * receiver and S the source interpolation.  It runs the forward kernels
+ * backwards in time on w = B lambda.
+ *
+ *   rec_resid [nshots][nt][nrec]  input traces (residuals) at the receivers.
+ *   src_grad  [nshots][nt][nsrc]  output: adjoint source wavelets.
+ *   Other arguments, validation and errors as for acoustic_forward.
+ */
+fd_status acoustic_adjoint(const fd_grid *grid, int so, double dt, int nt, int nshots,
+                           const float *m, const float *damp, int nsrc, const float *src_xyz,
+                           float *src_grad, int nrec, const float *rec_xyz,
+                           const float *rec_resid, void *stream);
+
+/*
+ * acoustic_gradient -- gradient with respect to m of <rec_resid, d(m)>, where
+ * d(m) are acoustic_forward's traces (zero initial state), summed over shots.
+ * With rec_resid = d(m) - d_obs this is the FWI gradient of
+ * J(m) = 1/2 sum ||d(m) - d_obs||^2 (adjoint-state method):
+ *   grad m = -(1/dt^2) sum_{k=1}^{nt-1} w^k (u^k - 2u^{k-1} + u^{k-2}),
+ * w the adjoint of acoustic_adjoint.  The forward wavefield is checkpointed
+ * (both time levels) every `checkpoint_every` steps (0: round(sqrt(nt-1)))
+ * and recomputed segment by segment during the reverse sweep (the paper's
+ * time-subsampled save, Listing fd-4, used for inversion).
+ *
+ *   src_wav   [nshots][nt][nsrc]  source wavelets of the forward model.
+ *   rec_resid [nshots][nt][nrec]  residual traces.
+ *   grad_m    [nz][ny][nx]        output.
+ *   Device memory: 4 + K + 2 + 2 ceil((nt-1)/K) wavefield volumes, K the
+ *   checkpoint interval.  Other arguments as for acoustic_forward.
+ */
+fd_status acoustic_gradient(const fd_grid *grid, int so, double dt, int nt, int nshots,
+                            const float *m, const float *damp, int nsrc, const float *src_xyz,
+                            const float *src_wav, int nrec, const float *rec_xyz,
+                            const float *rec_resid, int checkpoint_every, float *grad_m,
+                            void *stream);
+
+/*
  * acoustic_forward_noalloc -- acoustic_forward for callers that cannot
  * allocate device memory.  The paper has no counterpart; this is a library
  * convenience.

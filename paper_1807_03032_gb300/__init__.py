@@ -19,8 +19,8 @@ import numpy as np
 from . import _native
 from ._native import FdError, stats_enable, stats_get, stats_reset, version  # noqa: F401
 
-__all__ = ["Grid", "acoustic_forward", "tti_forward", "FdError", "version", "stats_enable",
-           "stats_get", "stats_reset"]
+__all__ = ["Grid", "acoustic_forward", "acoustic_adjoint", "acoustic_gradient", "tti_forward",
+           "FdError", "version", "stats_enable", "stats_get", "stats_reset"]
 
 
 @dataclass(frozen=True)
@@ -141,3 +141,46 @@ def tti_forward(grid, so, dt, nt, m, eps, delta, theta, phi, src_xyz, src_wav, r
         _ptr(p_final, "p_final"), _ptr(r_final, "r_final"), _stream_for(m, rec_out, stream=stream))
     _native.check(st)
     return rec_out, p_final, r_final
+
+
+def acoustic_adjoint(grid, so, dt, nt, m, src_xyz, rec_xyz, rec_resid, damp=None, src_grad=None,
+                     stream=None):
+    """Adjoint of acoustic_forward's source-to-receiver map (C ABI
+    ``acoustic_adjoint``): residual traces [nshots][nt][nrec] -> adjoint source
+    wavelets [nshots][nt][nsrc] (allocated like ``m`` unless given)."""
+    g = _as_grid(grid)
+    nshots, nsrc = int(src_xyz.shape[0]), int(src_xyz.shape[1])
+    nrec = int(rec_xyz.shape[1])
+    if tuple(rec_resid.shape) != (nshots, nt, nrec):
+        raise ValueError("rec_resid must be [nshots][nt][nrec]")
+    if src_grad is None:
+        src_grad = _empty_like_kind(m, (nshots, nt, nsrc))
+    st = _native.load().acoustic_adjoint(
+        g.struct(), int(so), float(dt), int(nt), nshots, _ptr(m, "m"), _ptr(damp, "damp"), nsrc,
+        _ptr(src_xyz, "src_xyz"), _ptr(src_grad, "src_grad"), nrec, _ptr(rec_xyz, "rec_xyz"),
+        _ptr(rec_resid, "rec_resid"), _stream_for(m, src_grad, stream=stream))
+    _native.check(st)
+    return src_grad
+
+
+def acoustic_gradient(grid, so, dt, nt, m, src_xyz, src_wav, rec_xyz, rec_resid, damp=None,
+                      checkpoint_every=0, grad=None, stream=None):
+    """Gradient with respect to m of <rec_resid, d(m)> (C ABI
+    ``acoustic_gradient``), checkpointing the forward wavefield every
+    ``checkpoint_every`` steps (0: sqrt(nt-1)).  Returns [nz][ny][nx]."""
+    g = _as_grid(grid)
+    nshots, nsrc = int(src_xyz.shape[0]), int(src_xyz.shape[1])
+    nrec = int(rec_xyz.shape[1])
+    if tuple(rec_resid.shape) != (nshots, nt, nrec):
+        raise ValueError("rec_resid must be [nshots][nt][nrec]")
+    if tuple(src_wav.shape) != (nshots, nt, nsrc):
+        raise ValueError("src_wav must be [nshots][nt][nsrc]")
+    if grad is None:
+        grad = _empty_like_kind(m, tuple(g.shape))
+    st = _native.load().acoustic_gradient(
+        g.struct(), int(so), float(dt), int(nt), nshots, _ptr(m, "m"), _ptr(damp, "damp"), nsrc,
+        _ptr(src_xyz, "src_xyz"), _ptr(src_wav, "src_wav"), nrec, _ptr(rec_xyz, "rec_xyz"),
+        _ptr(rec_resid, "rec_resid"), int(checkpoint_every), _ptr(grad, "grad"),
+        _stream_for(m, grad, stream=stream))
+    _native.check(st)
+    return grad

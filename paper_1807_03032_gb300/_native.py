@@ -24,7 +24,8 @@ STATUS_NAMES = {
 # Every symbol include/fdsweep.h declares (checked by the ABI test).
 EXPORTED = ("acoustic_forward", "tti_forward", "fd_last_error", "fd_version",
             "fd_stats_enable", "fd_stats_reset", "fd_stats_get", "fd_set_acoustic_config",
-            "fd_num_acoustic_configs", "fd_launch_count", "acoustic_forward_noalloc")
+            "fd_num_acoustic_configs", "fd_launch_count", "acoustic_forward_noalloc",
+            "acoustic_adjoint", "acoustic_gradient")
 
 
 class FdGrid(ctypes.Structure):
@@ -63,6 +64,10 @@ def load(path: str = LIB_PATH):
         lib.acoustic_forward.restype = I
         lib.acoustic_forward_noalloc.argtypes = [G, I, D, I, I, P, P, I, P, P, I, P, P, P, P, P]
         lib.acoustic_forward_noalloc.restype = I
+        lib.acoustic_adjoint.argtypes = [G, I, D, I, I, P, P, I, P, P, I, P, P, P]
+        lib.acoustic_adjoint.restype = I
+        lib.acoustic_gradient.argtypes = [G, I, D, I, I, P, P, I, P, P, I, P, P, I, P, P]
+        lib.acoustic_gradient.restype = I
         lib.tti_forward.argtypes = [G, I, D, I, I, P, P, P, P, P, P, I, P, P, I, P, P, P, P, P,
                                     P, P]
         lib.tti_forward.restype = I

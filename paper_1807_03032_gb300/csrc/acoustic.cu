@@ -131,7 +131,8 @@ __global__ void __launch_bounds__(TX *TY)
     const int za = chunk * zchunk;
     const int zb = min(a.L.nz, za + zchunk);
     const int nplanes = zb - za + 2 * R;  // arriving planes za-R .. zb+R-1
-    const int wcur = 2 * shot + a.cur, wprev = 2 * shot + 1 - a.cur;
+    const int wcur = shot * a.lps + a.lev_cur, wprev = shot * a.lps + a.lev_prev;
+    const int wout = shot * a.lps + a.lev_out;
     const int gx = x0 + 4 * tx;
 
     if (tid == 0) {
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(TX *TY)
         yok[v] = gy[v] < a.L.ny;
         dpyv[v] = yok[v] ? a.dpy[gy[v]] : 0.f;
     }
-    float *__restrict__ unew = a.wave + (int64_t)wprev * a.L.vol;
+    float *__restrict__ unew = a.wave + (int64_t)wout * a.L.vol;
     const f2 one2 = f2_splat(1.f);
 
     // acc[i][v]: pending output plane p - R + i (p = arriving plane)
@@ -398,8 +399,8 @@ int acoustic_default_config(int radius) {
     return 0;
 }
 
-fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots, float *wave,
-                        const float *bcoef, AcousticPlan *plan) {
+fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots, int lps,
+                        float *wave, const float *bcoef, AcousticPlan *plan) {
     int n = 0;
     const ConfigEntry *tab = config_table(radius, &n);
     if (!tab) return set_error(FD_ERR_SO, "no acoustic kernel for radius %d", radius);
@@ -441,10 +442,10 @@ fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots,
     if (plan->smem > e.smem)
         FD_CUDA_TRY(cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)plan->smem));
-    FD_TRY(make_tensor_map_4d(&plan->map_halo, wave, L.nx, L.ny, L.nz, 2ull * nshots,
+    FD_TRY(make_tensor_map_4d(&plan->map_halo, wave, L.nx, L.ny, L.nz, (uint64_t)nshots * lps,
                               (uint64_t)L.nxp * 4, (uint64_t)L.plane * 4, (uint64_t)L.vol * 4,
                               e.pw, e.ph, 1, 1));
-    FD_TRY(make_tensor_map_4d(&plan->map_int, wave, L.nx, L.ny, L.nz, 2ull * nshots,
+    FD_TRY(make_tensor_map_4d(&plan->map_int, wave, L.nx, L.ny, L.nz, (uint64_t)nshots * lps,
                               (uint64_t)L.nxp * 4, (uint64_t)L.plane * 4, (uint64_t)L.vol * 4,
                               e.bx, e.by, 1, 1));
     return make_tensor_map_4d(&plan->map_b, bcoef, L.nx, L.ny, L.nz, 1, (uint64_t)L.nxp * 4,

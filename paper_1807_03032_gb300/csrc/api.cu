@@ -347,7 +347,7 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     // ---- K1 plan and arguments
     AcousticPlan plan;
     FD_STAGE(s, "acoustic: initial state");
-    FD_TRY(acoustic_plan(R, g_acoustic_config[R], L, nshots, wave, bcoef, &plan));
+    FD_TRY(acoustic_plan(R, g_acoustic_config[R], L, nshots, 2, wave, bcoef, &plan));
     FD_STAGE(s, plan.name);
     AcousticStepArgs a;
     memset(&a, 0, sizeof(a));
@@ -379,6 +379,10 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     sp.src_tab = src_tab;
     sp.src_wav = swav.dev;
     sp.inj_level1 = -1;
+    sp.inj_t0 = 0;
+    sp.inj_dt = 1;
+    sp.rec_t0 = 0;
+    sp.rec_dt = 1;
     sp.nrec = nrec;
     sp.rec_tab = rec_tab;
     sp.rec_out = srec.dev;
@@ -390,7 +394,7 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     if (timing) FD_TRY(evs.create(nsteps, 3));
     auto step = [&](int i, int par, bool via_counter) -> fd_status {
         AcousticStepArgs ai = a;
-        ai.cur = par;
+        set_two_levels(ai, par);
         if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 0), s));
         FD_TRY(acoustic_launch(plan, ai, s));
         if (!via_counter && trace_level() >= 2) FD_STAGE(s, "acoustic_step kernel");
@@ -559,6 +563,10 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
     sp.nsrc = nsrc;
     sp.src_tab = src_tab;
     sp.src_wav = swav.dev;
+    sp.inj_t0 = 0;
+    sp.inj_dt = 1;
+    sp.rec_t0 = 0;
+    sp.rec_dt = 1;
     sp.nrec = nrec;
     sp.rec_tab = rec_tab;
     sp.rec_out = srec.dev;
@@ -623,6 +631,348 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
     return flags_to_status(hs.flags, "tti_forward");
 }
 
+// ====================================================================== adjoint
+
+// Shared setup of the acoustic adjoint and gradient: b, damping, sparse
+// tables, validation and the stability check (the same bound as forward).
+static fd_status acoustic_common_setup(const fd_grid *grid, int so, double dt, const GridDerived &gd,
+                                       int nshots, const float *m, const float *damp, int nsrc,
+                                       const float *src_xyz, int nrec, const float *rec_xyz,
+                                       float *bcoef, float *dps, SparsePoint *src_tab,
+                                       SparsePoint *rec_tab, MediumStats *dstats,
+                                       const char *what, cudaStream_t s) {
+    const WaveLayout &L = gd.L;
+    FD_CUDA_TRY(cudaMemsetAsync(bcoef, 0, (size_t)L.vol * 4, s));
+    FD_TRY(init_medium_stats(dstats, s));
+    FD_TRY(setup_acoustic_coeffs(m, damp, dt, L, bcoef, dps, dstats, s));
+    for (int sh = 0; sh < nshots; ++sh) {
+        FD_TRY(setup_sparse_table(src_xyz ? src_xyz + (size_t)sh * nsrc * 3 : nullptr, nsrc,
+                                  *grid, L, src_tab + (size_t)sh * nsrc, &dstats->flags, s));
+        FD_TRY(setup_sparse_table(rec_xyz ? rec_xyz + (size_t)sh * nrec * 3 : nullptr, nrec,
+                                  *grid, L, rec_tab + (size_t)sh * nrec, &dstats->flags, s));
+    }
+    FD_TRY(finish_medium_stats(dstats, s));
+    MediumStats hs;
+    FD_TRY(read_stats(dstats, &hs, s));
+    FD_TRY(flags_to_status(hs.flags, what));
+    const double vmax = 1.0 / sqrt((double)hs.m_min);
+    const double sig = second_symbol_max(so / 2, gd.w);
+    const double lam = sig * (1.0 / (grid->hx * grid->hx) + 1.0 / (grid->hy * grid->hy) +
+                              1.0 / (grid->hz * grid->hz));
+    const double dt_max = 2.0 / (vmax * sqrt(lam));
+    if (dt > dt_max * (1.0 + 1e-12))
+        return set_error(FD_ERR_CFL, "%s: dt = %.6g ms exceeds the stability bound %.6g ms", what,
+                         dt, dt_max);
+    return FD_OK;
+}
+
+static void fill_step_args(AcousticStepArgs &a, const fd_grid *grid, const GridDerived &gd,
+                           float *wave, const float *bcoef, const float *dps, int nshots,
+                           unsigned int *err) {
+    const WaveLayout &L = gd.L;
+    memset(&a, 0, sizeof(a));
+    a.wave = wave;
+    a.bcoef = bcoef;
+    a.dpx = dps;
+    a.dpy = dps + L.nx;
+    a.dpz = dps + L.nx + L.ny;
+    a.L = L;
+    a.nshots = nshots;
+    a.err = err;
+    const double ih2[3] = {1.0 / (grid->hx * grid->hx), 1.0 / (grid->hy * grid->hy),
+                           1.0 / (grid->hz * grid->hz)};
+    a.wc = (float)(gd.w[0] * (ih2[0] + ih2[1] + ih2[2]));
+    for (int k = 1; k <= kMaxRadius; ++k) {
+        a.wx[k] = (float)(gd.w[k] * ih2[0]);
+        a.wy[k] = (float)(gd.w[k] * ih2[1]);
+        a.wz[k] = (float)(gd.w[k] * ih2[2]);
+    }
+}
+
+/*
+ * Adjoint of the source-to-receiver map (zero initial state).  With the
+ * scaled adjoint variable w = b * lambda, the exact discrete adjoint
+ *   lambda^n = R^T dd^n + M1^T lambda^{n+1} - M2^T lambda^{n+2}
+ * becomes w^n = M1 w^{n+1} - M2 w^{n+2} + B R^T dd^n -- the forward update --
+ * so the adjoint runs the forward machinery backwards in time: residuals are
+ * injected at the receivers (scaled by b, like a source) and the gradient for
+ * source sample n is the interpolation of w^{n+1} at the sources.
+ */
+static fd_status acoustic_adjoint_impl(const fd_grid *grid, int so, double dt, int nt, int nshots,
+                                       const float *m, const float *damp, int nsrc,
+                                       const float *src_xyz, float *src_grad, int nrec,
+                                       const float *rec_xyz, const float *rec_resid,
+                                       cudaStream_t caller) {
+    FD_TRY(validate_common(grid, so, dt, nt, nshots, m, nsrc, src_xyz, src_grad, nrec, rec_xyz,
+                           rec_resid));
+    const int R = so / 2;
+    GridDerived gd = derive(grid, so);
+    const WaveLayout &L = gd.L;
+    const size_t dense = (size_t)L.nx * L.ny * L.nz;
+    const int ndamp = L.nx + L.ny + L.nz;
+    CallStream cs;
+    FD_TRY(cs.begin(caller));
+    cudaStream_t s = cs.get();
+    Workspace ws;
+    float *wave, *bcoef, *dps;
+    SparsePoint *src_tab, *rec_tab;
+    MediumStats *dstats;
+    int *counter;
+    ws.add(&wave, (size_t)2 * nshots * L.vol);
+    ws.add(&bcoef, L.vol);
+    ws.add(&dps, ndamp);
+    ws.add(&src_tab, (size_t)nshots * nsrc);
+    ws.add(&rec_tab, (size_t)nshots * nrec);
+    ws.add(&dstats, 1);
+    ws.add(&counter, 1);
+    Staged sm, sdamp, ssxyz, srxyz, sres;
+    StagedOut sgrad;
+    sm.plan(ws, m, dense);
+    sdamp.plan(ws, damp, damp ? ndamp : 0);
+    ssxyz.plan(ws, src_xyz, (size_t)nshots * nsrc * 3);
+    srxyz.plan(ws, rec_xyz, (size_t)nshots * nrec * 3);
+    sres.plan(ws, rec_resid, (size_t)nshots * nt * nrec);
+    sgrad.plan(ws, src_grad, (size_t)nshots * nt * nsrc);
+    FD_TRY(ws.allocate(s));
+    for (Staged *st : {&sm, &sdamp, &ssxyz, &srxyz, &sres}) FD_TRY(st->place(s));
+    FD_TRY(acoustic_common_setup(grid, so, dt, gd, nshots, sm.dev, sdamp.dev, nsrc, ssxyz.dev,
+                                 nrec, srxyz.dev, bcoef, dps, src_tab, rec_tab, dstats,
+                                 "acoustic_adjoint", s));
+    FD_CUDA_TRY(cudaMemsetAsync(wave, 0, (size_t)2 * nshots * L.vol * 4, s));
+    if (sgrad.dev && nsrc > 0)
+        FD_CUDA_TRY(cudaMemsetAsync(sgrad.dev, 0, (size_t)nshots * nt * nsrc * 4, s));
+    AcousticPlan plan;
+    FD_TRY(acoustic_plan(R, g_acoustic_config[R], L, nshots, 2, wave, bcoef, &plan));
+    AcousticStepArgs a;
+    fill_step_args(a, grid, gd, wave, bcoef, dps, nshots, &dstats->flags);
+    // sparse roles swapped: inject residuals at the receivers, sample at the sources
+    SparseArgs sp;
+    memset(&sp, 0, sizeof(sp));
+    sp.wave = wave;
+    sp.fields_per_shot = 2;
+    sp.L = L;
+    sp.bcoef = bcoef;
+    sp.nshots = nshots;
+    sp.nt = nt;
+    sp.nsrc = nrec;
+    sp.src_tab = rec_tab;
+    sp.src_wav = sres.dev;
+    sp.inj_level1 = -1;
+    sp.nrec = nsrc;
+    sp.rec_tab = src_tab;
+    sp.rec_out = sgrad.dev;
+    // w^{nt-1} = B R^T dd^{nt-1}
+    {
+        SparseArgs si = sp;
+        si.inj_level0 = 0;
+        si.inj_t0 = nt - 1;
+        si.inj_dt = 0;
+        FD_TRY(sparse_launch(si, 0, nrec > 0, false, s));
+    }
+    // reversed step i: w~^{i+1} = K1(w~^i, w~^{i-1}) + B R^T dd^{nt-2-i};
+    // dq^{nt-2-i} = S w~^i
+    const int nsteps = nt - 1;
+    auto step = [&](int i, int par, bool via_counter) -> fd_status {
+        AcousticStepArgs ai = a;
+        set_two_levels(ai, par);
+        FD_TRY(acoustic_launch(plan, ai, s));
+        SparseArgs si = sp;
+        si.inj_level0 = 1 - par;
+        si.rec_level = par;
+        si.inj_t0 = nt - 2;
+        si.inj_dt = -1;
+        si.rec_t0 = nt - 2;
+        si.rec_dt = -1;
+        si.step_base = via_counter ? counter : nullptr;
+        FD_TRY(sparse_launch(si, i, nrec > 0, nsrc > 0, s));
+        return FD_OK;
+    };
+    FD_TRY(run_time_loop(nsteps, s, counter, trace_level() < 2, step));
+    FD_STAGE(s, "adjoint: time loop");
+    FD_TRY(check_finite(wave, L, 2 * nshots, &dstats->flags, s));
+    FD_TRY(sgrad.copy_back(s));
+    MediumStats hs;
+    FD_TRY(read_stats(dstats, &hs, s));
+    ws.release();
+    FD_TRY(cs.finish());
+    return flags_to_status(hs.flags, "acoustic_adjoint");
+}
+
+// ====================================================================== gradient
+
+/*
+ * FWI gradient: grad m = d<dd, d(m)>/dm, summed over shots.  Forward with a
+ * checkpoint (u^t, u^{t-1}) every K steps; then, segment by segment from the
+ * last, the forward states of the segment are recomputed from its checkpoint
+ * and the adjoint w (see acoustic_adjoint) is stepped back through it while
+ *   grad += w^k (u^k - 2 u^{k-1} + u^{k-2}),   k = nt-1 .. 1,
+ * and finally grad *= -1/dt^2 (du^k/dm = -(u^k - 2u^{k-1} + u^{k-2})/(m+eta)
+ * and w = dt^2/(m+eta) lambda).
+ */
+static fd_status acoustic_gradient_impl(const fd_grid *grid, int so, double dt, int nt,
+                                        int nshots, const float *m, const float *damp, int nsrc,
+                                        const float *src_xyz, const float *src_wav, int nrec,
+                                        const float *rec_xyz, const float *rec_resid,
+                                        int checkpoint_every, float *grad_m,
+                                        cudaStream_t caller) {
+    FD_TRY(validate_common(grid, so, dt, nt, nshots, m, nsrc, src_xyz, src_wav, nrec, rec_xyz,
+                           rec_resid));
+    if (!grad_m) return set_error(FD_ERR_ARG, "acoustic_gradient: grad_m is null");
+    if (checkpoint_every < 0) return set_error(FD_ERR_ARG, "checkpoint_every must be >= 0");
+    const int R = so / 2;
+    GridDerived gd = derive(grid, so);
+    const WaveLayout &L = gd.L;
+    const size_t dense = (size_t)L.nx * L.ny * L.nz;
+    const int ndamp = L.nx + L.ny + L.nz;
+    const int nsteps = nt - 1;
+    int K = checkpoint_every > 0 ? checkpoint_every : (int)lround(sqrt((double)(nsteps > 1 ? nsteps : 1)));
+    if (K < 1) K = 1;
+    if (nsteps > 0 && K > nsteps) K = nsteps;
+    const int nseg = nsteps > 0 ? (nsteps + K - 1) / K : 0;
+    CallStream cs;
+    FD_TRY(cs.begin(caller));
+    cudaStream_t s = cs.get();
+    Workspace ws;
+    float *fwd, *adj, *seg, *ckpt, *grad, *bcoef, *dps;
+    SparsePoint *src_tab, *rec_tab;
+    MediumStats *dstats;
+    ws.add(&fwd, (size_t)2 * L.vol);
+    ws.add(&adj, (size_t)2 * L.vol);
+    ws.add(&seg, (size_t)(K + 2) * L.vol);
+    ws.add(&ckpt, (size_t)2 * (nseg > 0 ? nseg : 1) * L.vol);
+    ws.add(&grad, L.vol);
+    ws.add(&bcoef, L.vol);
+    ws.add(&dps, ndamp);
+    ws.add(&src_tab, (size_t)nshots * nsrc);
+    ws.add(&rec_tab, (size_t)nshots * nrec);
+    ws.add(&dstats, 1);
+    Staged sm, sdamp, ssxyz, swav, srxyz, sres;
+    StagedOut sg;
+    sm.plan(ws, m, dense);
+    sdamp.plan(ws, damp, damp ? ndamp : 0);
+    ssxyz.plan(ws, src_xyz, (size_t)nshots * nsrc * 3);
+    swav.plan(ws, src_wav, (size_t)nshots * nt * nsrc);
+    srxyz.plan(ws, rec_xyz, (size_t)nshots * nrec * 3);
+    sres.plan(ws, rec_resid, (size_t)nshots * nt * nrec);
+    sg.plan(ws, grad_m, dense);
+    FD_TRY(ws.allocate(s));
+    for (Staged *st : {&sm, &sdamp, &ssxyz, &swav, &srxyz, &sres}) FD_TRY(st->place(s));
+    FD_TRY(acoustic_common_setup(grid, so, dt, gd, nshots, sm.dev, sdamp.dev, nsrc, ssxyz.dev,
+                                 nrec, srxyz.dev, bcoef, dps, src_tab, rec_tab, dstats,
+                                 "acoustic_gradient", s));
+    FD_CUDA_TRY(cudaMemsetAsync(grad, 0, (size_t)L.vol * 4, s));
+    AcousticPlan pf, pa, ps;
+    FD_TRY(acoustic_plan(R, g_acoustic_config[R], L, 1, 2, fwd, bcoef, &pf));
+    FD_TRY(acoustic_plan(R, g_acoustic_config[R], L, 1, 2, adj, bcoef, &pa));
+    FD_TRY(acoustic_plan(R, g_acoustic_config[R], L, 1, K + 2, seg, bcoef, &ps));
+    AcousticStepArgs af, aa, as;
+    fill_step_args(af, grid, gd, fwd, bcoef, dps, 1, &dstats->flags);
+    fill_step_args(aa, grid, gd, adj, bcoef, dps, 1, &dstats->flags);
+    fill_step_args(as, grid, gd, seg, bcoef, dps, 1, &dstats->flags);
+    const size_t vb = (size_t)L.vol * 4;
+    for (int sh = 0; sh < nshots && nsteps > 0; ++sh) {
+        // sources of this shot injected into a one-shot buffer set
+        SparseArgs src;
+        memset(&src, 0, sizeof(src));
+        src.L = L;
+        src.bcoef = bcoef;
+        src.nshots = 1;
+        src.nt = nt;
+        src.nsrc = nsrc;
+        src.src_tab = src_tab + (size_t)sh * nsrc;
+        src.src_wav = swav.dev ? swav.dev + (size_t)sh * nt * nsrc : nullptr;
+        src.inj_level1 = -1;
+        src.inj_dt = 1;
+        src.rec_dt = 1;
+        SparseArgs res = src;  // residuals injected at the receivers
+        res.nsrc = nrec;
+        res.src_tab = rec_tab + (size_t)sh * nrec;
+        res.src_wav = sres.dev + (size_t)sh * nt * nrec;
+        // 1. forward with checkpoints
+        FD_CUDA_TRY(cudaMemsetAsync(fwd, 0, 2 * vb, s));
+        for (int t = 0; t < nsteps; ++t) {
+            const int cur = t & 1;
+            if (t % K == 0) {
+                const int c = t / K;
+                FD_CUDA_TRY(cudaMemcpyAsync(ckpt + (size_t)(2 * c) * L.vol, fwd + (size_t)(1 - cur) * L.vol,
+                                            vb, cudaMemcpyDeviceToDevice, s));
+                FD_CUDA_TRY(cudaMemcpyAsync(ckpt + (size_t)(2 * c + 1) * L.vol, fwd + (size_t)cur * L.vol,
+                                            vb, cudaMemcpyDeviceToDevice, s));
+            }
+            AcousticStepArgs ai = af;
+            set_two_levels(ai, cur);
+            FD_TRY(acoustic_launch(pf, ai, s));
+            SparseArgs si = src;
+            si.wave = fwd;
+            si.fields_per_shot = 2;
+            si.inj_level0 = 1 - cur;
+            FD_TRY(sparse_launch(si, t, nsrc > 0, false, s));
+        }
+        // 2. adjoint state: w^{nt-1} = B R^T dd^{nt-1} in level acur, w^{nt} = 0
+        FD_CUDA_TRY(cudaMemsetAsync(adj, 0, 2 * vb, s));
+        int acur = 0;
+        {
+            SparseArgs si = res;
+            si.wave = adj;
+            si.fields_per_shot = 2;
+            si.inj_level0 = acur;
+            si.inj_t0 = nt - 1;
+            si.inj_dt = 0;
+            FD_TRY(sparse_launch(si, 0, nrec > 0, false, s));
+        }
+        // 3. segments from the last
+        for (int c = nseg - 1; c >= 0; --c) {
+            const int t0 = c * K;
+            const int kmax = (c + 1) * K < nsteps ? (c + 1) * K : nsteps;
+            // seg level l holds u^{t0 - 1 + l}
+            FD_CUDA_TRY(cudaMemcpyAsync(seg, ckpt + (size_t)(2 * c) * L.vol, 2 * vb,
+                                        cudaMemcpyDeviceToDevice, s));
+            for (int t = t0 + 1; t <= kmax; ++t) {
+                AcousticStepArgs ai = as;
+                ai.lps = K + 2;
+                ai.lev_cur = t - t0;
+                ai.lev_prev = t - t0 - 1;
+                ai.lev_out = t - t0 + 1;
+                FD_TRY(acoustic_launch(ps, ai, s));
+                SparseArgs si = src;
+                si.wave = seg;
+                si.fields_per_shot = K + 2;
+                si.inj_level0 = t - t0 + 1;
+                FD_TRY(sparse_launch(si, t - 1, nsrc > 0, false, s));
+            }
+            for (int k = kmax; k >= t0 + 1; --k) {
+                const float *uk = seg + (size_t)(k - t0 + 1) * L.vol;
+                FD_TRY(grad_accumulate(grad, adj + (size_t)acur * L.vol, uk, uk - L.vol,
+                                       uk - 2 * L.vol, L.vol, s));
+                if (k >= 2) {
+                    // w^{k-1} = M1 w^k - M2 w^{k+1} + B R^T dd^{k-1}
+                    AcousticStepArgs ai = aa;
+                    set_two_levels(ai, acur);
+                    FD_TRY(acoustic_launch(pa, ai, s));
+                    SparseArgs si = res;
+                    si.wave = adj;
+                    si.fields_per_shot = 2;
+                    si.inj_level0 = 1 - acur;
+                    si.inj_t0 = k - 1;
+                    si.inj_dt = 0;
+                    FD_TRY(sparse_launch(si, 0, nrec > 0, false, s));
+                    acur = 1 - acur;
+                }
+            }
+        }
+        FD_STAGE(s, "gradient: shot done");
+    }
+    FD_TRY(scale_field(grad, (float)(-1.0 / (dt * dt)), L.vol, s));
+    FD_TRY(check_finite(grad, L, 1, &dstats->flags, s));
+    FD_TRY(copy_field_out(sg.dev, grad, L, s));
+    FD_TRY(sg.copy_back(s));
+    MediumStats hs;
+    FD_TRY(read_stats(dstats, &hs, s));
+    ws.release();
+    FD_TRY(cs.finish());
+    return flags_to_status(hs.flags, "acoustic_gradient");
+}
+
 }  // namespace fdsweep
 
 // ====================================================================== C ABI
@@ -649,6 +999,27 @@ fd_status tti_forward(const fd_grid *grid, int so, double dt, int nt, int nshots
     return fdsweep::tti_forward_impl(grid, so, dt, nt, nshots, m, damp, epsilon, delta, theta,
                                      phi, nsrc, src_xyz, src_wav, nrec, rec_xyz, rec_out, p_init,
                                      r_init, p_final, r_final, static_cast<cudaStream_t>(stream));
+}
+
+fd_status acoustic_adjoint(const fd_grid *grid, int so, double dt, int nt, int nshots,
+                           const float *m, const float *damp, int nsrc, const float *src_xyz,
+                           float *src_grad, int nrec, const float *rec_xyz,
+                           const float *rec_resid, void *stream) {
+    fdsweep::clear_error();
+    return fdsweep::acoustic_adjoint_impl(grid, so, dt, nt, nshots, m, damp, nsrc, src_xyz,
+                                          src_grad, nrec, rec_xyz, rec_resid,
+                                          static_cast<cudaStream_t>(stream));
+}
+
+fd_status acoustic_gradient(const fd_grid *grid, int so, double dt, int nt, int nshots,
+                            const float *m, const float *damp, int nsrc, const float *src_xyz,
+                            const float *src_wav, int nrec, const float *rec_xyz,
+                            const float *rec_resid, int checkpoint_every, float *grad_m,
+                            void *stream) {
+    fdsweep::clear_error();
+    return fdsweep::acoustic_gradient_impl(grid, so, dt, nt, nshots, m, damp, nsrc, src_xyz,
+                                           src_wav, nrec, rec_xyz, rec_resid, checkpoint_every,
+                                           grad_m, static_cast<cudaStream_t>(stream));
 }
 
 const char *fd_last_error(void) { return fdsweep::last_error(); }

@@ -40,7 +40,10 @@ struct AcousticStepArgs {
     const float *dpz;     // damp_z / dt, [nz]
     WaveLayout L;
     int nshots;
-    int cur;              // level holding u^n (u^{n-1} and u^{n+1} share the other)
+    // Buffer index of a level: shot * lps + level.  u^n is read from lev_cur,
+    // u^{n-1} from lev_prev, u^{n+1} written to lev_out (== lev_prev for the
+    // in-place two-level scheme; distinct when a history is being kept).
+    int lps, lev_cur, lev_prev, lev_out;
     float wc;             // sum over axes of w_0 / h_d^2
     float wx[kMaxRadius + 1], wy[kMaxRadius + 1], wz[kMaxRadius + 1];  // w_k / h_d^2
     unsigned int *err;
@@ -58,10 +61,19 @@ struct AcousticPlan {
     const char *name = "";
 };
 
+// Two-level in-place scheme: u^n in level `cur`, u^{n-1} and u^{n+1} in 1 - cur.
+inline void set_two_levels(AcousticStepArgs &a, int cur) {
+    a.lps = 2;
+    a.lev_cur = cur;
+    a.lev_prev = 1 - cur;
+    a.lev_out = 1 - cur;
+}
+
 int acoustic_num_configs(int radius);
 int acoustic_default_config(int radius);
-fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots, float *wave,
-                        const float *bcoef, AcousticPlan *plan);
+// `lps` levels per shot are addressable (buffers nshots * lps).
+fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots, int lps,
+                        float *wave, const float *bcoef, AcousticPlan *plan);
 fd_status acoustic_launch(const AcousticPlan &plan, const AcousticStepArgs &args,
                           cudaStream_t stream);
 
@@ -78,6 +90,10 @@ struct SparseArgs {
     const SparsePoint *src_tab;  // [nshots][nsrc]
     const float *src_wav;        // [nshots][nt][nsrc]
     int inj_level0, inj_level1;
+    // wavelet sample injected at step n: inj_t0 + inj_dt * n; trace sample
+    // written at step n: rec_t0 + rec_dt * n (forward: 0 + n; adjoint runs
+    // reversed time: nt - 2 - n)
+    int inj_t0, inj_dt, rec_t0, rec_dt;
     // interpolation of level `rec_level`
     int nrec;
     const SparsePoint *rec_tab;  // [nshots][nrec]
@@ -91,6 +107,11 @@ struct SparseArgs {
 fd_status sparse_launch(const SparseArgs &a, int step, bool do_inject, bool do_interp,
                         cudaStream_t stream);
 fd_status bump_counter(int *counter, int by, cudaStream_t stream);
+// grad += w * (u0 - 2 u1 + u2) over `n` floats (the FWI imaging condition of
+// one time step; scaled by -1/dt^2 once at the end).
+fd_status grad_accumulate(float *grad, const float *w, const float *u0, const float *u1,
+                          const float *u2, int64_t n, cudaStream_t stream);
+fd_status scale_field(float *f, float s, int64_t n, cudaStream_t stream);
 
 // ---------------------------------------------------------------- setup K0
 

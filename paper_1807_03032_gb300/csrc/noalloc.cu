@@ -199,7 +199,7 @@ fd_status noalloc_impl(const fd_grid *g, int so, double dt, int nt, int nshots, 
                                               (size_t)L.ny * L.nz, cudaMemcpyDeviceToDevice, s));
 
     AcousticPlan plan;
-    FD_TRY(acoustic_plan(R, -1, L, nshots, wave, bcoef, &plan));
+    FD_TRY(acoustic_plan(R, -1, L, nshots, 2, wave, bcoef, &plan));
     AcousticStepArgs a;
     memset(&a, 0, sizeof(a));
     a.wave = wave;
@@ -228,15 +228,19 @@ fd_status noalloc_impl(const fd_grid *g, int so, double dt, int nt, int nshots, 
     sp.src_tab = src_tab;
     sp.src_wav = src_wav;
     sp.inj_level1 = -1;
+    sp.inj_t0 = 0;
+    sp.inj_dt = 1;
+    sp.rec_t0 = 0;
+    sp.rec_dt = 1;
     sp.nrec = nrec;
     sp.rec_tab = rec_tab;
     sp.rec_out = rec_out;
     sp.step_base = nullptr;
     for (int n = 0; n + 1 < nt; ++n) {
-        a.cur = n & 1;
+        set_two_levels(a, n & 1);
         FD_TRY(acoustic_launch(plan, a, s));
-        sp.inj_level0 = 1 - a.cur;
-        sp.rec_level = a.cur;
+        sp.inj_level0 = 1 - (n & 1);
+        sp.rec_level = n & 1;
         FD_TRY(sparse_launch(sp, n, nsrc > 0, nrec > 0, s));
     }
     const int last = (nt - 1) & 1;

@@ -28,9 +28,10 @@ __device__ __forceinline__ int64_t corner_offset(const SparsePoint &p, int c, co
 // injecting); the following nshots*nsrc*8 threads inject.
 __global__ void sparse_kernel(const SparseArgs a, int step, int do_inject, int64_t nrec_total) {
     const int n = step + (a.step_base ? *a.step_base : 0);
-    if (n < 0 || n >= a.nt) return;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid < nrec_total) {
+        const int ro = a.rec_t0 + a.rec_dt * n;
+        if (ro < 0 || ro >= a.nt) return;
         const int s = (int)(gid / a.nrec);
         const int i = (int)(gid - (int64_t)s * a.nrec);
         const SparsePoint p = a.rec_tab[gid];
@@ -38,7 +39,7 @@ __global__ void sparse_kernel(const SparseArgs a, int step, int do_inject, int64
         float acc = 0.f;
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc = fmaf(corner_weight(p, c), __ldg(u + corner_offset(p, c, a.L)), acc);
-        a.rec_out[((int64_t)s * a.nt + n) * a.nrec + i] = acc;
+        a.rec_out[((int64_t)s * a.nt + ro) * a.nrec + i] = acc;
         return;
     }
     if (!do_inject) return;
@@ -48,9 +49,11 @@ __global__ void sparse_kernel(const SparseArgs a, int step, int do_inject, int64
     const int64_t ps = k >> 3;  // (shot, source)
     const int s = (int)(ps / a.nsrc);
     const int isrc = (int)(ps - (int64_t)s * a.nsrc);
+    const int qi = a.inj_t0 + a.inj_dt * n;
+    if (qi < 0 || qi >= a.nt) return;
     const SparsePoint p = a.src_tab[ps];
     const int64_t off = corner_offset(p, c, a.L);
-    const float q = a.src_wav[((int64_t)s * a.nt + n) * a.nsrc + isrc];
+    const float q = a.src_wav[((int64_t)s * a.nt + qi) * a.nsrc + isrc];
     const float val = corner_weight(p, c) * __ldg(a.bcoef + off) * q;
     atomicAdd(a.wave + (int64_t)(s * a.fields_per_shot + a.inj_level0) * a.L.vol + off, val);
     if (a.inj_level1 >= 0)
@@ -58,6 +61,39 @@ __global__ void sparse_kernel(const SparseArgs a, int step, int do_inject, int64
 }
 
 __global__ void bump_kernel(int *counter, int by) { *counter += by; }
+
+__global__ void grad_kernel(float *__restrict__ g, const float *__restrict__ w,
+                            const float *__restrict__ u0, const float *__restrict__ u1,
+                            const float *__restrict__ u2, int64_t n4) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = reinterpret_cast<const float4 *>(w)[i];
+        const float4 p = reinterpret_cast<const float4 *>(u0)[i];
+        const float4 q = reinterpret_cast<const float4 *>(u1)[i];
+        const float4 r = reinterpret_cast<const float4 *>(u2)[i];
+        float4 o = reinterpret_cast<float4 *>(g)[i];
+        o.x = fmaf(a.x, p.x - 2.f * q.x + r.x, o.x);
+        o.y = fmaf(a.y, p.y - 2.f * q.y + r.y, o.y);
+        o.z = fmaf(a.z, p.z - 2.f * q.z + r.z, o.z);
+        o.w = fmaf(a.w, p.w - 2.f * q.w + r.w, o.w);
+        reinterpret_cast<float4 *>(g)[i] = o;
+    }
+}
+
+__global__ void scale_kernel(float *__restrict__ f, float s, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        f[i] *= s;
+}
+
+int stream_grid(int64_t n, int threads) {
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int64_t b = (n + threads - 1) / threads;
+    if (b > (int64_t)nsm * 16) b = (int64_t)nsm * 16;
+    return (int)(b < 1 ? 1 : b);
+}
 
 }  // namespace
 
@@ -78,6 +114,22 @@ fd_status sparse_launch(const SparseArgs &a, int step, bool do_inject, bool do_i
 
 fd_status bump_counter(int *counter, int by, cudaStream_t stream) {
     bump_kernel<<<1, 1, 0, stream>>>(counter, by);
+    FD_CUDA_TRY(cudaGetLastError());
+    note_launch(stream);
+    return FD_OK;
+}
+
+fd_status grad_accumulate(float *grad, const float *w, const float *u0, const float *u1,
+                          const float *u2, int64_t n, cudaStream_t stream) {
+    if (n % 4) return set_error(FD_ERR_ARG, "grad_accumulate: length not a multiple of 4");
+    grad_kernel<<<stream_grid(n / 4, 256), 256, 0, stream>>>(grad, w, u0, u1, u2, n / 4);
+    FD_CUDA_TRY(cudaGetLastError());
+    note_launch(stream);
+    return FD_OK;
+}
+
+fd_status scale_field(float *f, float s, int64_t n, cudaStream_t stream) {
+    scale_kernel<<<stream_grid(n, 256), 256, 0, stream>>>(f, s, n);
     FD_CUDA_TRY(cudaGetLastError());
     note_launch(stream);
     return FD_OK;
