@@ -321,6 +321,12 @@ def run_ours(args):
         torch.cuda.empty_cache()
         tti = run_tti(args, fd, _native, dev, stream, peak)
 
+    # ---------------------------------------------------------------- FWI gradient
+    fwi = None
+    if not args.no_fwi:
+        torch.cuda.empty_cache()
+        fwi = run_fwi(args, fd, dev, stream)
+
     # ---------------------------------------------------------------- CPU baseline (oracle)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -346,6 +352,7 @@ def run_ours(args):
             "e2e": e2e,
             "cpu_baseline": cpu,
             "tti": tti,
+            "fwi_gradient": fwi,
             "clocks": clocks,
             "gpu_launches": int(launches),
         }
@@ -396,6 +403,51 @@ def run_tti(args, fd, _native, dev, stream, peak):
                                   "pass2_ms": round(p2[0] / max(p2[1], 1), 4),
                                   "hbm_frac_44B": round(gb / peak, 4)}
     return out
+
+
+def run_fwi(args, fd, dev, stream):
+    """FWI gradient on the 256^3 layered model: 16 shots, 256 x 256 receivers,
+    so = 8, nt = 2000, checkpoint every 45 steps.  Timed: the forward model of
+    all shots in the initial model, the residual, and the checkpointed
+    adjoint-state gradient."""
+    import torch
+    n, nt, nshots, K = args.fwi_n, args.fwi_nt, 16, 45
+    t0 = time.time()
+    true, init = workloads.fwi_layered(n=n, so=8, nt=nt, nshots=nshots)
+    log(f"[bench] FWI workload built in {time.time() - t0:.1f}s")
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    g = fd.Grid(init.shape, init.spacing, init.origin)
+    mt, m0, damp, sx, sw, rx = (T(a) for a in (true.m, init.m, init.damp, init.src_xyz,
+                                               init.src_wav, init.rec_xyz))
+    dobs, _ = fd.acoustic_forward(g, 8, init.dt, nt, mt, sx, sw, rx, damp=damp,
+                                  return_final=False)
+    # warm-up on a short window
+    fd.acoustic_gradient(g, 8, init.dt, 40, m0, sx[:1], sw[:1, :40].contiguous(), rx[:1],
+                         dobs[:1, :40].contiguous(), damp=damp, checkpoint_every=7)
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    dpred, _ = fd.acoustic_forward(g, 8, init.dt, nt, m0, sx, sw, rx, damp=damp,
+                                   return_final=False)
+    resid = dpred - dobs
+    e1.record(stream)
+    grad = fd.acoustic_gradient(g, 8, init.dt, nt, m0, sx, sw, rx, resid, damp=damp,
+                                checkpoint_every=K)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms, grad_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    pts = float(init.npoints) * (nt - 1) * nshots
+    ok = bool(torch.isfinite(grad).all())
+    return {"workload": f"FWI gradient {n}^3 layered 1.5-3.5 km/s (initial = true smoothed "
+                        f"sigma 10), so 8, nt {nt}, {nshots} shots, {n}x{n} receivers, "
+                        f"checkpoint every {K}",
+            "forward_gpts": round(pts / (fwd_ms * 1e-3) / 1e9, 2),
+            "gradient_gpts": round(pts / (grad_ms * 1e-3) / 1e9, 2),
+            "gradient_s": round(grad_ms * 1e-3, 3), "forward_s": round(fwd_ms * 1e-3, 3),
+            "objective": float(0.5 * (resid.double() ** 2).sum()), "finite": ok,
+            "note": "gradient GPts/s counts forward-model grid-point updates (nt-1 per shot); "
+                    "the gradient performs a forward with checkpoints, a recomputation and "
+                    "an adjoint sweep"}
 
 
 def cpu_baseline(w, so_list):
@@ -469,6 +521,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tti", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fwi", action="store_true")
+    ap.add_argument("--fwi-n", type=int, default=256)
+    ap.add_argument("--fwi-nt", type=int, default=2000)
     args = ap.parse_args()
     args.so = tuple(args.so)
     if args.impl == "reference":

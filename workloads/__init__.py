@@ -259,3 +259,42 @@ def tti_small(so=4, nt=100, n=48, h=10.0, nbl=8, seed=7):
                     slowness_squared(v), damping_profile(shape, nbl, (h, h, h), 2.5),
                     _f32(src), _f32(wav), _f32(rec), nbl=nbl, eps=eps, delta=delta,
                     theta=theta, phi=phi)
+
+
+def fwi_layered(n=256, so=8, nt=2000, nshots=16, h=20.0, nbl=40, receivers_per_side=None,
+                smooth_sigma=10.0, f0=0.010):
+    """FWI gradient problem: a 4-layer true model (1.5, 2.0, 2.75, 3.5 km/s,
+    equal thicknesses below the top border), the initial model is the true one
+    Gaussian-smoothed (sigma = 10 points); shots on a 4 x 4 grid 20 m below the
+    top border; receivers on a full surface grid half a cell below the border.
+    Returns (true, initial) Workloads sharing the geometry."""
+    shape = (n, n, n)
+    v = np.empty(shape, dtype=np.float64)
+    layers = (1.5, 2.0, 2.75, 3.5)
+    edges = np.linspace(nbl, n, len(layers) + 1).astype(int)
+    v[: edges[1]] = layers[0]
+    for i, vel in enumerate(layers):
+        v[edges[i]:edges[i + 1]] = vel
+    # the model varies with depth only, so the 3-D Gaussian smoothing is the
+    # 1-D smoothing of the depth profile (edges held constant, no wrap)
+    from scipy.ndimage import gaussian_filter1d
+    prof0 = gaussian_filter1d(v[:, 0, 0], smooth_sigma, mode="nearest")
+    v0 = np.broadcast_to(prof0[:, None, None], shape).copy()
+    vmax = max(layers)
+    dt = cfl_dt((h, h, h), vmax)
+    side = int(round(math.sqrt(nshots)))
+    xs = np.linspace(nbl * h, (n - 1 - nbl) * h, side + 2)[1:-1]
+    sx, sy = np.meshgrid(xs, xs, indexing="ij")
+    src = np.stack([sx.ravel(), sy.ravel(), np.full(side * side, nbl * h + 20.0)], -1)[:, None, :]
+    r = n if receivers_per_side is None else receivers_per_side
+    gx = np.linspace(0.0, (n - 1) * h, r)
+    gy, gx = np.meshgrid(gx, gx, indexing="ij")
+    rec = np.stack([gx.ravel(), gy.ravel(), np.full(r * r, nbl * h + 0.5 * h)], -1)
+    rec = np.tile(rec[None], (src.shape[0], 1, 1))
+    wav = np.tile(ricker(nt, dt, f0=f0)[None, :, None], (src.shape[0], 1, 1))
+    damp = damping_profile(shape, nbl, (h, h, h), vmax)
+    true = Workload(f"fwi-true-{n}^3", shape, (h, h, h), (0.0, 0.0, 0.0), so, dt, nt,
+                    slowness_squared(v), damp, _f32(src), _f32(wav), _f32(rec), nbl=nbl)
+    init = Workload(f"fwi-init-{n}^3", shape, (h, h, h), (0.0, 0.0, 0.0), so, dt, nt,
+                    slowness_squared(v0), damp, _f32(src), _f32(wav), _f32(rec), nbl=nbl)
+    return true, init
