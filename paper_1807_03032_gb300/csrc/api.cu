@@ -533,6 +533,8 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
         if (r_init) FD_TRY(copy_fields_in(wave, L, r_init, sh, 2, 4, 2, s));
     }
 
+    TtiPlan tplan;
+    FD_TRY(tti_plan(R, L, nshots, wave, tmp, bcoef, &tplan));
     TtiArgs a;
     memset(&a, 0, sizeof(a));
     a.wave = wave;
@@ -581,7 +583,7 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
         cudaEvent_t ev3[3];
         if (timing)
             for (int k = 0; k < 3; ++k) ev3[k] = evs.at(i, k);
-        FD_TRY(tti_launch(R, ai, s, nullptr, nullptr, timing ? ev3 : nullptr));
+        FD_TRY(tti_launch(tplan, ai, s, timing ? ev3 : nullptr));
         SparseArgs si = sp;
         si.inj_level0 = 1 - par;
         si.inj_level1 = 3 - par;

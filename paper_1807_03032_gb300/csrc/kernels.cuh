@@ -152,7 +152,20 @@ struct TtiArgs {
     unsigned int *err;
 };
 
-fd_status tti_launch(int radius, const TtiArgs &a, cudaStream_t stream, float *ms_pass1,
-                     float *ms_pass2, cudaEvent_t *ev /* 3 events or null */);
+struct TtiPlan {
+    int radius = 0;
+    CUtensorMap map_wint, map_whalo;          // p/r buffers: interior, x+y halo boxes
+    CUtensorMap map_tint, map_tx, map_ty;     // temporaries: interior, x-halo, y-halo
+    CUtensorMap map_cint;                     // b, a, s, n_x, n_y, n_z: interior box
+    dim3 grid, block;
+    size_t smem1 = 0, smem2 = 0;
+    int zchunk = 0, nzc = 1;
+};
+
+// coef: 6 consecutive fields b, a, s, n_x, n_y, n_z ([6][vol]).
+fd_status tti_plan(int radius, const WaveLayout &L, int nshots, float *wave, float *tmp,
+                   const float *coef, TtiPlan *plan);
+fd_status tti_launch(const TtiPlan &plan, const TtiArgs &a, cudaStream_t stream,
+                     cudaEvent_t *ev /* 3 events or null */);
 
 }  // namespace fdsweep

@@ -16,116 +16,504 @@
 //   q+ = q + (1 - zeta)(q - q-) + b * rhs_q,  b = dt^2/(m + damp dt/2),
 //   zeta = damp * b / dt.
 // Temporaries outside the grid are zero ghosts, like the fields.
+//
+// GB300 design (both passes, like the acoustic step): one CTA owns a BX x BY
+// column and marches it through z.  The z-derivatives use an accumulator
+// pipeline (2R pending outputs per point in registers, fed by the interior
+// tile of each arriving plane); the x/y derivatives of the output plane
+// s = p - R come from tiles staged with their halo.  Every operand arrives by
+// cp.async.bulk.tensor into a (D+1)-slot ring with full/empty mbarriers.  The
+// CTA has two thread groups: in K2a one differentiates p and the other r; in
+// K2b one builds A = Hxy p and the other B = Hz r, they exchange A and B
+// through shared memory, and update p and r respectively.
 #include "kernels.cuh"
 
 namespace fdsweep {
 namespace {
 
-constexpr int TBX = 32, TBY = 8;
+template <int R, int TX, int TY, int D>
+struct TtiCfg {
+    static constexpr int BX = 4 * TX;
+    static constexpr int BY = TY;
+    static constexpr int RA = (R + 3) / 4 * 4;
+    static constexpr int PW = BX + 2 * RA;       // x-halo width
+    static constexpr int PH = BY + 2 * R;        // y-halo height
+    static constexpr int NSL = D + 1;
+    static constexpr int GROUP = TX * TY;        // threads per group
+    static constexpr int THREADS = 2 * GROUP;
+    static constexpr int WARPS = THREADS / 32;
+    static constexpr int INT = BX * BY;
+    static constexpr int HXY = (PW * PH + 31) / 32 * 32;  // x+y halo tile
+    static constexpr int HX = (PW * BY + 31) / 32 * 32;   // x-halo tile
+    static constexpr int HY = (BX * PH + 31) / 32 * 32;   // y-halo tile
+    // pass 1 stage: [p(j)][r(j)] interiors, [p(s)][r(s)] xy-halo, [nx][ny][nz](s)
+    static constexpr int STAGE1 = 2 * INT + 2 * HXY + 3 * INT;
+    // pass 2 stage: [fz(j)][ez(j)], [fx(s)][ex(s)] x-halo, [fy(s)][ey(s)] y-halo,
+    //               [p][p-][r][r-][b][a][s](s)
+    static constexpr int STAGE2 = 2 * INT + 2 * HX + 2 * HY + 7 * INT;
+    static constexpr size_t SMEM1 = (size_t)NSL * STAGE1 * 4 + NSL * 16 + 16 + 128;
+    static constexpr size_t SMEM2 = (size_t)NSL * STAGE2 * 4 + 4 * INT * 4 + NSL * 16 + 16 + 128;
+    static_assert(PW <= 256 && PH <= 256, "TMA box dimension limit");
+    static_assert(GROUP % 32 == 0, "thread groups must be whole warps");
+};
 
-template <int R>
-__device__ __forceinline__ float dfirst(const float *__restrict__ f, int64_t q, int64_t stride,
-                                        int idx, int n, const float *c) {
-    // sum_k c_k (f[idx+k] - f[idx-k]) with zero ghosts outside [0, n)
-    float d = 0.f;
+__device__ __forceinline__ float4 f4add(float4 a, float4 b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ float4 f4fma(float w, float4 a, float4 c) {
+    return make_float4(fmaf(w, a.x, c.x), fmaf(w, a.y, c.y), fmaf(w, a.z, c.z), fmaf(w, a.w, c.w));
+}
+__device__ __forceinline__ float4 lds4(const float *p) {
+    return *reinterpret_cast<const float4 *>(p);
+}
+
+// First derivative along x of 4 consecutive points from a row that starts RA
+// points left of them: sum_k c_k (q[+k] - q[-k]).
+template <int R, int RA>
+__device__ __forceinline__ float4 dx4(const float *row, const float *c) {
+    float xs[2 * RA + 4];
+#pragma unroll
+    for (int t = 0; t < (2 * RA + 4) / 4; ++t) {
+        const float4 f = lds4(row + 4 * t);
+        xs[4 * t] = f.x;
+        xs[4 * t + 1] = f.y;
+        xs[4 * t + 2] = f.z;
+        xs[4 * t + 3] = f.w;
+    }
+    float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int k = 1; k <= R; ++k) {
-        const float fp = (idx + k < n) ? __ldg(f + q + k * stride) : 0.f;
-        const float fm = (idx - k >= 0) ? __ldg(f + q - k * stride) : 0.f;
-        d = fmaf(c[k], fp - fm, d);
+        d.x = fmaf(c[k], xs[RA + 0 + k] - xs[RA + 0 - k], d.x);
+        d.y = fmaf(c[k], xs[RA + 1 + k] - xs[RA + 1 - k], d.y);
+        d.z = fmaf(c[k], xs[RA + 2 + k] - xs[RA + 2 - k], d.z);
+        d.w = fmaf(c[k], xs[RA + 3 + k] - xs[RA + 3 - k], d.w);
     }
     return d;
 }
 
+// First derivative along y: `centre` points at the thread's float4 in the
+// centre row, rows `pitch` floats apart.
 template <int R>
-__global__ void __launch_bounds__(TBX *TBY) tti_pass1_kernel(const TtiArgs a) {
-    const int i = blockIdx.x * TBX + threadIdx.x;
-    const int j = blockIdx.y * TBY + threadIdx.y;
-    const int k = blockIdx.z % a.L.nz;
-    const int s = blockIdx.z / a.L.nz;
-    if (i >= a.L.nx || j >= a.L.ny) return;
-    const WaveLayout &L = a.L;
-    const int64_t q = (int64_t)k * L.plane + (int64_t)j * L.nxp + i;
-    const float *p = a.wave + (int64_t)(4 * s + a.cur) * L.vol;
-    const float *r = a.wave + (int64_t)(4 * s + 2 + a.cur) * L.vol;
-    const float gpx = dfirst<R>(p, q, 1, i, L.nx, a.cx);
-    const float gpy = dfirst<R>(p, q, L.nxp, j, L.ny, a.cy);
-    const float gpz = dfirst<R>(p, q, L.plane, k, L.nz, a.cz);
-    const float grx = dfirst<R>(r, q, 1, i, L.nx, a.cx);
-    const float gry = dfirst<R>(r, q, L.nxp, j, L.ny, a.cy);
-    const float grz = dfirst<R>(r, q, L.plane, k, L.nz, a.cz);
-    const float nx = __ldg(a.nvec + q), ny = __ldg(a.nvec + L.vol + q),
-                nz = __ldg(a.nvec + 2 * L.vol + q);
-    const float hp = nx * gpx + ny * gpy + nz * gpz;
-    const float hr = nx * grx + ny * gry + nz * grz;
-    float *t = a.tmp + (int64_t)6 * s * L.vol;
-    t[q] = gpx - nx * hp;
-    t[L.vol + q] = gpy - ny * hp;
-    t[2 * L.vol + q] = gpz - nz * hp;
-    t[3 * L.vol + q] = nx * hr;
-    t[4 * L.vol + q] = ny * hr;
-    t[5 * L.vol + q] = nz * hr;
+__device__ __forceinline__ float4 dy4(const float *centre, int pitch, const float *c) {
+    float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 1; k <= R; ++k) {
+        const float4 p = lds4(centre + k * pitch), m = lds4(centre - k * pitch);
+        d.x = fmaf(c[k], p.x - m.x, d.x);
+        d.y = fmaf(c[k], p.y - m.y, d.y);
+        d.z = fmaf(c[k], p.z - m.z, d.z);
+        d.w = fmaf(c[k], p.w - m.w, d.w);
+    }
+    return d;
 }
 
+// z first-derivative accumulator pipeline: acc[i] is output plane p-R+i when
+// plane p arrives with values c.  Returns nothing; acc[0] is then complete.
 template <int R>
-__global__ void __launch_bounds__(TBX *TBY) tti_pass2_kernel(const TtiArgs a) {
-    const int i = blockIdx.x * TBX + threadIdx.x;
-    const int j = blockIdx.y * TBY + threadIdx.y;
-    const int k = blockIdx.z % a.L.nz;
-    const int s = blockIdx.z / a.L.nz;
-    if (i >= a.L.nx || j >= a.L.ny) return;
-    const WaveLayout &L = a.L;
-    const int64_t q = (int64_t)k * L.plane + (int64_t)j * L.nxp + i;
-    const float *t = a.tmp + (int64_t)6 * s * L.vol;
-    const float A = dfirst<R>(t, q, 1, i, L.nx, a.cx) +
-                    dfirst<R>(t + L.vol, q, L.nxp, j, L.ny, a.cy) +
-                    dfirst<R>(t + 2 * L.vol, q, L.plane, k, L.nz, a.cz);
-    const float B = dfirst<R>(t + 3 * L.vol, q, 1, i, L.nx, a.cx) +
-                    dfirst<R>(t + 4 * L.vol, q, L.nxp, j, L.ny, a.cy) +
-                    dfirst<R>(t + 5 * L.vol, q, L.plane, k, L.nz, a.cz);
-    float *p = a.wave + (int64_t)(4 * s + a.cur) * L.vol;
-    float *pn = a.wave + (int64_t)(4 * s + 1 - a.cur) * L.vol;
-    float *r = a.wave + (int64_t)(4 * s + 2 + a.cur) * L.vol;
-    float *rn = a.wave + (int64_t)(4 * s + 3 - a.cur) * L.vol;
-    const float b = __ldg(a.bcoef + q), av = __ldg(a.acoef + q), sv = __ldg(a.scoef + q);
-    const float zeta = (a.dpx[i] + a.dpy[j] + a.dpz[k]) * b;
-    const float pc = p[q], pm = pn[q], rc = r[q], rm = rn[q];
-    pn[q] = pc + (1.f - zeta) * (pc - pm) + b * (av * A + sv * B);
-    rn[q] = rc + (1.f - zeta) * (rc - rm) + b * (sv * A + B);
+__device__ __forceinline__ void dz_feed(float4 (&acc)[2 * R], float4 c, const float *cz) {
+#pragma unroll
+    for (int i = 0; i < 2 * R; ++i) {
+        if (i == R) continue;
+        const float w = i < R ? cz[R - i] : -cz[i - R];
+        acc[i] = f4fma(w, c, acc[i]);
+    }
+}
+template <int R>
+__device__ __forceinline__ void dz_shift(float4 (&acc)[2 * R], float4 c, const float *cz) {
+#pragma unroll
+    for (int i = 0; i < 2 * R - 1; ++i) acc[i] = acc[i + 1];
+    const float w = -cz[R];
+    acc[2 * R - 1] = make_float4(w * c.x, w * c.y, w * c.z, w * c.w);
 }
 
+struct Ring {
+    float *smem;
+    uint64_t *full, *empty;
+    volatile int *abort_flag;
+};
+
+template <int NSL, int WARPS>
+__device__ __forceinline__ Ring ring_init(unsigned char *raw, size_t stage_floats, int extra_floats) {
+    Ring r;
+    r.smem = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(raw) + 127) &
+                                       ~static_cast<uintptr_t>(127));
+    r.full = reinterpret_cast<uint64_t *>(r.smem + NSL * stage_floats + extra_floats);
+    r.empty = r.full + NSL;
+    r.abort_flag = reinterpret_cast<volatile int *>(r.empty + NSL);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSL; ++s) {
+            mbar_init(&r.full[s], 1);
+            mbar_init(&r.empty[s], WARPS);
+        }
+        fence_mbar_init();
+        *r.abort_flag = 0;
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------- pass 1
+
+template <int R, int TX, int TY, int D>
+__global__ void __launch_bounds__(2 * TX * TY)
+    tti_pass1_kernel(const __grid_constant__ CUtensorMap map_wint,
+                     const __grid_constant__ CUtensorMap map_whalo,
+                     const __grid_constant__ CUtensorMap map_cint, const TtiArgs a, int zchunk,
+                     int nzc) {
+    using C = TtiCfg<R, TX, TY, D>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Ring ring = ring_init<C::NSL, C::WARPS>(smem_raw, C::STAGE1, 0);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int field = tid / C::GROUP;  // 0: p, 1: r
+    const int t = tid - field * C::GROUP;
+    const int tx = t % TX, ty = t / TX;
+    const int shot = blockIdx.z / nzc, chunk = blockIdx.z - shot * nzc;
+    const int x0 = blockIdx.x * C::BX, y0 = blockIdx.y * C::BY;
+    const int za = chunk * zchunk, zb = min(a.L.nz, za + zchunk);
+    const int nplanes = zb - za + 2 * R;
+    const int wp = 4 * shot + a.cur, wr = 4 * shot + 2 + a.cur;
+    __syncthreads();
+
+    int issued = 0;
+    auto issue = [&](int jj) -> bool {
+        const int slot = jj % C::NSL;
+        if (jj >= C::NSL &&
+            !mbar_wait_bounded(&ring.empty[slot], (uint32_t)(((jj - C::NSL) / C::NSL) & 1)))
+            return false;
+        const bool out = jj >= 2 * R;
+        const uint32_t bytes = 2 * C::INT * 4 + (out ? (2 * C::PW * C::PH + 3 * C::INT) * 4 : 0);
+        mbar_arrive_expect_tx(&ring.full[slot], bytes);
+        float *st = ring.smem + slot * C::STAGE1;
+        const int zj = za - R + jj;
+        tma_load_4d(st, &map_wint, &ring.full[slot], x0, y0, zj, wp);
+        tma_load_4d(st + C::INT, &map_wint, &ring.full[slot], x0, y0, zj, wr);
+        if (out) {
+            const int zs = zj - R;
+            float *h = st + 2 * C::INT;
+            tma_load_4d(h, &map_whalo, &ring.full[slot], x0 - C::RA, y0 - R, zs, wp);
+            tma_load_4d(h + C::HXY, &map_whalo, &ring.full[slot], x0 - C::RA, y0 - R, zs, wr);
+            float *n = h + 2 * C::HXY;
+            for (int c = 0; c < 3; ++c)
+                tma_load_4d(n + c * C::INT, &map_cint, &ring.full[slot], x0, y0, zs, 3 + c);
+        }
+        issued = jj + 1;
+        return true;
+    };
+    if (tid == 0)
+        for (int jj = 0; jj < D && jj < nplanes; ++jj) issue(jj);
+
+    const int gx = x0 + 4 * tx, gy = y0 + ty;
+    const bool ok = gx < a.L.nxp && gy < a.L.ny;
+    float *out = a.tmp + (int64_t)(6 * shot + 3 * field) * a.L.vol;
+    float4 acc[2 * R];
+#pragma unroll
+    for (int i = 0; i < 2 * R; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool failed = false;
+    for (int j = 0; j < nplanes; ++j) {
+        if (tid == 0 && j + D < nplanes && !failed && !issue(j + D)) {
+            failed = true;
+            *ring.abort_flag = 1;
+            atomicOr(a.err, DEV_ERR_TIMEOUT);
+        }
+        const int slot = j % C::NSL;
+        if (*ring.abort_flag ||
+            !mbar_wait_bounded(&ring.full[slot], (uint32_t)((j / C::NSL) & 1))) {
+            *ring.abort_flag = 1;
+            atomicOr(a.err, DEV_ERR_TIMEOUT);
+            break;
+        }
+        const float *st = ring.smem + slot * C::STAGE1;
+        const int q = ty * C::BX + 4 * tx;
+        const float4 c = lds4(st + field * C::INT + q);
+        dz_feed<R>(acc, c, a.cz);
+        if (j >= 2 * R) {
+            const int zs = za - 2 * R + j;
+            const float *H = st + 2 * C::INT + field * C::HXY;
+            const float4 gxv = dx4<R, C::RA>(H + (R + ty) * C::PW + 4 * tx, a.cx);
+            const float4 gyv = dy4<R>(H + (R + ty) * C::PW + C::RA + 4 * tx, C::PW, a.cy);
+            const float4 gzv = acc[0];
+            const float *N = st + 2 * C::INT + 2 * C::HXY;
+            const float4 nx = lds4(N + q), ny = lds4(N + C::INT + q), nz = lds4(N + 2 * C::INT + q);
+            float4 h;
+            h.x = nx.x * gxv.x + ny.x * gyv.x + nz.x * gzv.x;
+            h.y = nx.y * gxv.y + ny.y * gyv.y + nz.y * gzv.y;
+            h.z = nx.z * gxv.z + ny.z * gyv.z + nz.z * gzv.z;
+            h.w = nx.w * gxv.w + ny.w * gyv.w + nz.w * gzv.w;
+            float4 o0, o1, o2;
+            if (field == 0) {  // f_i = g_i - n_i h
+                o0 = make_float4(gxv.x - nx.x * h.x, gxv.y - nx.y * h.y, gxv.z - nx.z * h.z, gxv.w - nx.w * h.w);
+                o1 = make_float4(gyv.x - ny.x * h.x, gyv.y - ny.y * h.y, gyv.z - ny.z * h.z, gyv.w - ny.w * h.w);
+                o2 = make_float4(gzv.x - nz.x * h.x, gzv.y - nz.y * h.y, gzv.z - nz.z * h.z, gzv.w - nz.w * h.w);
+            } else {  // e_i = n_i h
+                o0 = make_float4(nx.x * h.x, nx.y * h.y, nx.z * h.z, nx.w * h.w);
+                o1 = make_float4(ny.x * h.x, ny.y * h.y, ny.z * h.z, ny.w * h.w);
+                o2 = make_float4(nz.x * h.x, nz.y * h.y, nz.z * h.z, nz.w * h.w);
+            }
+            if (ok) {
+                const int64_t off = (int64_t)zs * a.L.plane + (int64_t)gy * a.L.nxp + gx;
+                *reinterpret_cast<float4 *>(out + off) = o0;
+                *reinterpret_cast<float4 *>(out + a.L.vol + off) = o1;
+                *reinterpret_cast<float4 *>(out + 2 * a.L.vol + off) = o2;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ring.empty[slot]);
+        dz_shift<R>(acc, c, a.cz);
+    }
+    __syncthreads();
+    if (*ring.abort_flag && tid == 0)
+        for (int jj = issued - C::NSL; jj < issued; ++jj)
+            if (jj >= 0)
+                mbar_wait_bounded(&ring.full[jj % C::NSL], (uint32_t)((jj / C::NSL) & 1), 200000000ull);
+}
+
+// ---------------------------------------------------------------- pass 2
+
+template <int R, int TX, int TY, int D>
+__global__ void __launch_bounds__(2 * TX * TY)
+    tti_pass2_kernel(const __grid_constant__ CUtensorMap map_tint,
+                     const __grid_constant__ CUtensorMap map_tx,
+                     const __grid_constant__ CUtensorMap map_ty,
+                     const __grid_constant__ CUtensorMap map_wint,
+                     const __grid_constant__ CUtensorMap map_cint, const TtiArgs a, int zchunk,
+                     int nzc) {
+    using C = TtiCfg<R, TX, TY, D>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Ring ring = ring_init<C::NSL, C::WARPS>(smem_raw, C::STAGE2, 4 * C::INT);
+    float *xchg = ring.smem + C::NSL * C::STAGE2;  // [2 buffers][A | B][INT]
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int field = tid / C::GROUP;  // 0: A = Hxy p (f), 1: B = Hz r (e)
+    const int t = tid - field * C::GROUP;
+    const int tx = t % TX, ty = t / TX;
+    const int shot = blockIdx.z / nzc, chunk = blockIdx.z - shot * nzc;
+    const int x0 = blockIdx.x * C::BX, y0 = blockIdx.y * C::BY;
+    const int za = chunk * zchunk, zb = min(a.L.nz, za + zchunk);
+    const int nplanes = zb - za + 2 * R;
+    const int tbase = 6 * shot;
+    const int wq = 4 * shot + 2 * field + a.cur, wqm = 4 * shot + 2 * field + 1 - a.cur;
+    __syncthreads();
+
+    int issued = 0;
+    auto issue = [&](int jj) -> bool {
+        const int slot = jj % C::NSL;
+        if (jj >= C::NSL &&
+            !mbar_wait_bounded(&ring.empty[slot], (uint32_t)(((jj - C::NSL) / C::NSL) & 1)))
+            return false;
+        const bool out = jj >= 2 * R;
+        const uint32_t bytes =
+            2 * C::INT * 4 + (out ? (2 * C::PW * C::BY + 2 * C::BX * C::PH + 7 * C::INT) * 4 : 0);
+        mbar_arrive_expect_tx(&ring.full[slot], bytes);
+        float *st = ring.smem + slot * C::STAGE2;
+        const int zj = za - R + jj;
+        tma_load_4d(st, &map_tint, &ring.full[slot], x0, y0, zj, tbase + 2);           // f_z
+        tma_load_4d(st + C::INT, &map_tint, &ring.full[slot], x0, y0, zj, tbase + 5);  // e_z
+        if (out) {
+            const int zs = zj - R;
+            float *hx = st + 2 * C::INT;
+            tma_load_4d(hx, &map_tx, &ring.full[slot], x0 - C::RA, y0, zs, tbase + 0);       // f_x
+            tma_load_4d(hx + C::HX, &map_tx, &ring.full[slot], x0 - C::RA, y0, zs, tbase + 3);  // e_x
+            float *hy = hx + 2 * C::HX;
+            tma_load_4d(hy, &map_ty, &ring.full[slot], x0, y0 - R, zs, tbase + 1);       // f_y
+            tma_load_4d(hy + C::HY, &map_ty, &ring.full[slot], x0, y0 - R, zs, tbase + 4);  // e_y
+            float *w = hy + 2 * C::HY;
+            const int wb = 4 * shot;
+            tma_load_4d(w, &map_wint, &ring.full[slot], x0, y0, zs, wb + a.cur);                   // p
+            tma_load_4d(w + C::INT, &map_wint, &ring.full[slot], x0, y0, zs, wb + 1 - a.cur);      // p-
+            tma_load_4d(w + 2 * C::INT, &map_wint, &ring.full[slot], x0, y0, zs, wb + 2 + a.cur);  // r
+            tma_load_4d(w + 3 * C::INT, &map_wint, &ring.full[slot], x0, y0, zs, wb + 3 - a.cur);  // r-
+            for (int c = 0; c < 3; ++c)  // b, a, s
+                tma_load_4d(w + (4 + c) * C::INT, &map_cint, &ring.full[slot], x0, y0, zs, c);
+        }
+        issued = jj + 1;
+        return true;
+    };
+    if (tid == 0)
+        for (int jj = 0; jj < D && jj < nplanes; ++jj) issue(jj);
+
+    const int gx = x0 + 4 * tx, gy = y0 + ty;
+    const bool ok = gx < a.L.nxp && gy < a.L.ny;
+    float dpx4[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) dpx4[i] = (gx + i < a.L.nx) ? a.dpx[gx + i] : 0.f;
+    const float dpy = gy < a.L.ny ? a.dpy[gy] : 0.f;
+    float *qn = a.wave + (int64_t)wqm * a.L.vol;  // q^{n+1} overwrites q^{n-1}
+    (void)wq;
+    float4 acc[2 * R];
+#pragma unroll
+    for (int i = 0; i < 2 * R; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool failed = false;
+    for (int j = 0; j < nplanes; ++j) {
+        if (tid == 0 && j + D < nplanes && !failed && !issue(j + D)) {
+            failed = true;
+            *ring.abort_flag = 1;
+            atomicOr(a.err, DEV_ERR_TIMEOUT);
+        }
+        const int slot = j % C::NSL;
+        bool good = !*ring.abort_flag &&
+                    mbar_wait_bounded(&ring.full[slot], (uint32_t)((j / C::NSL) & 1));
+        if (!good) {
+            *ring.abort_flag = 1;
+            atomicOr(a.err, DEV_ERR_TIMEOUT);
+        }
+        const float *st = ring.smem + slot * C::STAGE2;
+        const int q = ty * C::BX + 4 * tx;
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (good) {
+            c = lds4(st + field * C::INT + q);
+            dz_feed<R>(acc, c, a.cz);
+        }
+        const bool outp = j >= 2 * R;
+        float *xb = xchg + (j & 1) * 2 * C::INT;
+        if (outp && good) {
+            const float *hx = st + 2 * C::INT + field * C::HX;
+            const float *hy = st + 2 * C::INT + 2 * C::HX + field * C::HY;
+            const float4 dxv = dx4<R, C::RA>(hx + ty * C::PW + 4 * tx, a.cx);
+            const float4 dyv = dy4<R>(hy + (R + ty) * C::BX + 4 * tx, C::BX, a.cy);
+            const float4 v = f4add(f4add(dxv, dyv), acc[0]);  // A (field 0) or B (field 1)
+            *reinterpret_cast<float4 *>(xb + field * C::INT + q) = v;
+        }
+        // all threads (both groups) reach this barrier every iteration
+        if (outp) __syncthreads();
+        if (*ring.abort_flag) break;
+        if (outp) {
+            const int zs = za - 2 * R + j;
+            const float *w = st + 2 * C::INT + 2 * C::HX + 2 * C::HY;
+            const float4 A = lds4(xb + q), B = lds4(xb + C::INT + q);
+            const float4 qc = lds4(w + 2 * field * C::INT + q);
+            const float4 qm = lds4(w + (2 * field + 1) * C::INT + q);
+            const float4 b = lds4(w + 4 * C::INT + q), av = lds4(w + 5 * C::INT + q),
+                         sv = lds4(w + 6 * C::INT + q);
+            const float dyz = dpy + a.dpz[zs];
+            float4 rhs;
+            if (field == 0) {  // p: a A + s B
+                rhs = make_float4(av.x * A.x + sv.x * B.x, av.y * A.y + sv.y * B.y,
+                                  av.z * A.z + sv.z * B.z, av.w * A.w + sv.w * B.w);
+            } else {  // r: s A + B
+                rhs = make_float4(sv.x * A.x + B.x, sv.y * A.y + B.y, sv.z * A.z + B.z,
+                                  sv.w * A.w + B.w);
+            }
+            float4 o;
+            o.x = qc.x + (1.f - (dpx4[0] + dyz) * b.x) * (qc.x - qm.x) + b.x * rhs.x;
+            o.y = qc.y + (1.f - (dpx4[1] + dyz) * b.y) * (qc.y - qm.y) + b.y * rhs.y;
+            o.z = qc.z + (1.f - (dpx4[2] + dyz) * b.z) * (qc.z - qm.z) + b.z * rhs.z;
+            o.w = qc.w + (1.f - (dpx4[3] + dyz) * b.w) * (qc.w - qm.w) + b.w * rhs.w;
+            if (ok) {
+                const int64_t off = (int64_t)zs * a.L.plane + (int64_t)gy * a.L.nxp + gx;
+                *reinterpret_cast<float4 *>(qn + off) = o;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ring.empty[slot]);
+        dz_shift<R>(acc, c, a.cz);
+    }
+    __syncthreads();
+    if (*ring.abort_flag && tid == 0)
+        for (int jj = issued - C::NSL; jj < issued; ++jj)
+            if (jj >= 0)
+                mbar_wait_bounded(&ring.full[jj % C::NSL], (uint32_t)((jj / C::NSL) & 1), 200000000ull);
+}
+
+// ---------------------------------------------------------------- host side
+
+constexpr int kTX = 16, kTY = 8;  // 64 x 8 tile, two groups of 128 threads
+
 template <int R>
-fd_status launch_r(const TtiArgs &a, cudaStream_t stream, cudaEvent_t *ev) {
-    dim3 block(TBX, TBY, 1);
-    dim3 grid((a.L.nx + TBX - 1) / TBX, (a.L.ny + TBY - 1) / TBY, a.L.nz * a.nshots);
-    if (ev) FD_CUDA_TRY(cudaEventRecord(ev[0], stream));
-    tti_pass1_kernel<R><<<grid, block, 0, stream>>>(a);
-    FD_CUDA_TRY(cudaGetLastError());
-    note_launch(stream);
-    if (ev) FD_CUDA_TRY(cudaEventRecord(ev[1], stream));
-    tti_pass2_kernel<R><<<grid, block, 0, stream>>>(a);
-    FD_CUDA_TRY(cudaGetLastError());
-    note_launch(stream);
-    if (ev) FD_CUDA_TRY(cudaEventRecord(ev[2], stream));
-    return FD_OK;
+struct TtiKernels {
+    static constexpr int D = 2;
+    using C = TtiCfg<R, kTX, kTY, D>;
+    static const void *p1() { return (const void *)&tti_pass1_kernel<R, kTX, kTY, D>; }
+    static const void *p2() { return (const void *)&tti_pass2_kernel<R, kTX, kTY, D>; }
+};
+
+struct TtiInfo {
+    const void *p1, *p2;
+    size_t smem1, smem2;
+    int bx, by, pw, ph, threads;
+};
+
+template <int R>
+TtiInfo info_r() {
+    using K = TtiKernels<R>;
+    using C = typename K::C;
+    return TtiInfo{K::p1(), K::p2(), C::SMEM1, C::SMEM2, C::BX, C::BY, C::PW, C::PH, C::THREADS};
+}
+
+bool tti_info(int radius, TtiInfo *out) {
+    switch (radius) {
+        case 1: *out = info_r<1>(); return true;
+        case 2: *out = info_r<2>(); return true;
+        case 4: *out = info_r<4>(); return true;
+        case 6: *out = info_r<6>(); return true;
+        case 8: *out = info_r<8>(); return true;
+        default: return false;
+    }
 }
 
 }  // namespace
 
-fd_status tti_launch(int radius, const TtiArgs &a, cudaStream_t stream, float *ms_pass1,
-                     float *ms_pass2, cudaEvent_t *ev) {
-    (void)ms_pass1;
-    (void)ms_pass2;
-    if ((int64_t)a.L.nz * a.nshots > 65535)
-        return set_error(FD_ERR_ARG, "TTI launch: nz * nshots exceeds 65535");
-    switch (radius) {
-        case 1: return launch_r<1>(a, stream, ev);
-        case 2: return launch_r<2>(a, stream, ev);
-        case 4: return launch_r<4>(a, stream, ev);
-        case 6: return launch_r<6>(a, stream, ev);
-        case 8: return launch_r<8>(a, stream, ev);
-        default: return set_error(FD_ERR_SO, "no TTI kernel for radius %d", radius);
+fd_status tti_plan(int radius, const WaveLayout &L, int nshots, float *wave, float *tmp,
+                   const float *coef, TtiPlan *plan) {
+    TtiInfo in;
+    if (!tti_info(radius, &in)) return set_error(FD_ERR_SO, "no TTI kernel for radius %d", radius);
+    plan->radius = radius;
+    int dev = 0, nsm = 0, per_sm = 0;
+    FD_CUDA_TRY(cudaGetDevice(&dev));
+    FD_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    FD_CUDA_TRY(cudaFuncSetAttribute(in.p1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)in.smem1));
+    FD_CUDA_TRY(cudaFuncSetAttribute(in.p2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)in.smem2));
+    FD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, in.p2, in.threads, in.smem2));
+    if (per_sm < 1) return set_error(FD_ERR_CUDA, "TTI pass-2 kernel does not fit on an SM");
+    const int ntx = (L.nx + in.bx - 1) / in.bx, nty = (L.ny + in.by - 1) / in.by;
+    const int64_t cols = (int64_t)ntx * nty * nshots, slots = (int64_t)nsm * per_sm;
+    int nzc = 1;
+    if (cols < slots) {
+        nzc = (int)((slots + cols - 1) / cols);
+        const int min_chunk = 8 * radius > 32 ? 8 * radius : 32;
+        const int max_nzc = L.nz / min_chunk > 1 ? L.nz / min_chunk : 1;
+        if (nzc > max_nzc) nzc = max_nzc;
     }
+    const int zchunk = (L.nz + nzc - 1) / nzc;
+    nzc = (L.nz + zchunk - 1) / zchunk;
+    if ((int64_t)nshots * nzc > 65535 || nty > 65535)
+        return set_error(FD_ERR_ARG, "grid too large for the TTI launch configuration");
+    plan->grid = dim3(ntx, nty, nshots * nzc);
+    plan->block = dim3(in.threads, 1, 1);
+    plan->smem1 = in.smem1;
+    plan->smem2 = in.smem2;
+    plan->zchunk = zchunk;
+    plan->nzc = nzc;
+    const uint64_t sy = (uint64_t)L.nxp * 4, sz = (uint64_t)L.plane * 4, sw = (uint64_t)L.vol * 4;
+    FD_TRY(make_tensor_map_4d(&plan->map_wint, wave, L.nx, L.ny, L.nz, 4ull * nshots, sy, sz, sw,
+                              in.bx, in.by, 1, 1));
+    FD_TRY(make_tensor_map_4d(&plan->map_whalo, wave, L.nx, L.ny, L.nz, 4ull * nshots, sy, sz, sw,
+                              in.pw, in.ph, 1, 1));
+    FD_TRY(make_tensor_map_4d(&plan->map_tint, tmp, L.nx, L.ny, L.nz, 6ull * nshots, sy, sz, sw,
+                              in.bx, in.by, 1, 1));
+    FD_TRY(make_tensor_map_4d(&plan->map_tx, tmp, L.nx, L.ny, L.nz, 6ull * nshots, sy, sz, sw,
+                              in.pw, in.by, 1, 1));
+    FD_TRY(make_tensor_map_4d(&plan->map_ty, tmp, L.nx, L.ny, L.nz, 6ull * nshots, sy, sz, sw,
+                              in.bx, in.ph, 1, 1));
+    return make_tensor_map_4d(&plan->map_cint, coef, L.nx, L.ny, L.nz, 6, sy, sz, sw, in.bx,
+                              in.by, 1, 1);
+}
+
+fd_status tti_launch(const TtiPlan &plan, const TtiArgs &a, cudaStream_t stream,
+                     cudaEvent_t *ev) {
+    TtiInfo in;
+    if (!tti_info(plan.radius, &in)) return set_error(FD_ERR_SO, "bad TTI plan");
+    int zchunk = plan.zchunk, nzc = plan.nzc;
+    if (ev) FD_CUDA_TRY(cudaEventRecord(ev[0], stream));
+    void *p1[] = {(void *)&plan.map_wint, (void *)&plan.map_whalo, (void *)&plan.map_cint,
+                  (void *)&a, (void *)&zchunk, (void *)&nzc};
+    FD_CUDA_TRY(cudaLaunchKernel(in.p1, plan.grid, plan.block, p1, plan.smem1, stream));
+    note_launch(stream);
+    if (ev) FD_CUDA_TRY(cudaEventRecord(ev[1], stream));
+    void *p2[] = {(void *)&plan.map_tint, (void *)&plan.map_tx, (void *)&plan.map_ty,
+                  (void *)&plan.map_wint, (void *)&plan.map_cint, (void *)&a, (void *)&zchunk,
+                  (void *)&nzc};
+    FD_CUDA_TRY(cudaLaunchKernel(in.p2, plan.grid, plan.block, p2, plan.smem2, stream));
+    note_launch(stream);
+    if (ev) FD_CUDA_TRY(cudaEventRecord(ev[2], stream));
+    return FD_OK;
 }
 
 }  // namespace fdsweep
