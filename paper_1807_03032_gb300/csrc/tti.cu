@@ -416,12 +416,16 @@ __global__ void __launch_bounds__(2 * TX * TY)
 
 constexpr int kTX = 16, kTY = 8;  // 64 x 8 tile, two groups of 128 threads
 
+// Prefetch depth per pass: pass 2 stages carry eleven tiles, so for the wide
+// stencils one slot less keeps two CTAs per SM.
 template <int R>
 struct TtiKernels {
-    static constexpr int D = 2;
-    using C = TtiCfg<R, kTX, kTY, D>;
-    static const void *p1() { return (const void *)&tti_pass1_kernel<R, kTX, kTY, D>; }
-    static const void *p2() { return (const void *)&tti_pass2_kernel<R, kTX, kTY, D>; }
+    static constexpr int D1 = 2;
+    static constexpr int D2 = R >= 6 ? 1 : 2;
+    using C1 = TtiCfg<R, kTX, kTY, D1>;
+    using C2 = TtiCfg<R, kTX, kTY, D2>;
+    static const void *p1() { return (const void *)&tti_pass1_kernel<R, kTX, kTY, D1>; }
+    static const void *p2() { return (const void *)&tti_pass2_kernel<R, kTX, kTY, D2>; }
 };
 
 struct TtiInfo {
@@ -433,8 +437,11 @@ struct TtiInfo {
 template <int R>
 TtiInfo info_r() {
     using K = TtiKernels<R>;
-    using C = typename K::C;
-    return TtiInfo{K::p1(), K::p2(), C::SMEM1, C::SMEM2, C::BX, C::BY, C::PW, C::PH, C::THREADS};
+    using C1 = typename K::C1;
+    using C2 = typename K::C2;
+    static_assert(C1::BX == C2::BX && C1::BY == C2::BY && C1::THREADS == C2::THREADS, "tiles");
+    return TtiInfo{K::p1(), K::p2(), C1::SMEM1, C2::SMEM2, C1::BX, C1::BY, C1::PW, C1::PH,
+                   C1::THREADS};
 }
 
 bool tti_info(int radius, TtiInfo *out) {
