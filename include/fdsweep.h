@@ -212,6 +212,46 @@ fd_status acoustic_forward_noalloc(const fd_grid *grid, int so, double dt, int n
                                    const float *rec_xyz, float *rec_out, const float *u_init,
                                    float *u_final, void *stream);
 
+/*
+ * Batch engine for serving (no counterpart in the paper).
+ *
+ * Shots that share a velocity model (grid, so, dt, m, damp) are slots of one
+ * engine.  fd_engine_step advances every active slot by the same number of
+ * time steps with one stencil launch per step over all active slots (the
+ * shot is the outer dimension); chunks are captured into CUDA graphs and
+ * replayed while the set of active slots is unchanged.  A slot added at the
+ * engine's global step G starts from the zero state at its own time index
+ * n = 0 and runs the scheme of acoustic_forward (injection of src[n] into
+ * u^{n+1}, trace rec[n] = interp(u^n)), so its traces equal acoustic_forward's
+ * for the same shot; other slots may be at any time index.  Each engine owns
+ * a non-blocking CUDA stream (fd_engine_stream), so engines run concurrently.
+ * All memory is allocated by fd_engine_create (fd_engine_footprint gives the
+ * bytes); adding, stepping and releasing allocate nothing.  Pointers are
+ * device memory and must stay valid until the shot is released.
+ */
+typedef struct fd_engine fd_engine;
+fd_status fd_engine_footprint(const fd_grid *grid, int max_slots, int max_nsrc, int max_nrec,
+                              int64_t *bytes);
+fd_status fd_engine_create(const fd_grid *grid, int so, double dt, const float *m,
+                           const float *damp, int max_slots, int max_nsrc, int max_nrec,
+                           fd_engine **engine);
+/* src_wav [nt][nsrc], rec_out [nt][nrec]; *slot receives the slot index.
+ * FD_ERR_ARG if no slot is free or sizes exceed the engine's maxima. */
+fd_status fd_engine_add_shot(fd_engine *engine, int nt, int nsrc, const float *src_xyz,
+                             const float *src_wav, int nrec, const float *rec_xyz, float *rec_out,
+                             int *slot);
+/* Advance all active slots by nsteps (even, >= 0) time steps (asynchronous). */
+fd_status fd_engine_step(fd_engine *engine, int nsteps);
+/* Host-side view: whether the slot is active and how many of its time steps
+ * have not been enqueued yet (0: its last trace sample is enqueued; it is
+ * complete once the engine's stream has reached that point). */
+fd_status fd_engine_shot_status(fd_engine *engine, int slot, int *active, int64_t *steps_left);
+fd_status fd_engine_release(fd_engine *engine, int slot);
+fd_status fd_engine_stream(fd_engine *engine, void **stream);
+/* Wait for the engine's queued work and report device-side errors. */
+fd_status fd_engine_sync(fd_engine *engine);
+fd_status fd_engine_destroy(fd_engine *engine);
+
 /* Message describing the last error on the calling thread ("" if none). */
 const char *fd_last_error(void);
 

@@ -25,7 +25,9 @@ STATUS_NAMES = {
 EXPORTED = ("acoustic_forward", "tti_forward", "fd_last_error", "fd_version",
             "fd_stats_enable", "fd_stats_reset", "fd_stats_get", "fd_set_acoustic_config",
             "fd_num_acoustic_configs", "fd_launch_count", "acoustic_forward_noalloc",
-            "acoustic_adjoint", "acoustic_gradient")
+            "acoustic_adjoint", "acoustic_gradient", "fd_engine_footprint", "fd_engine_create",
+            "fd_engine_add_shot", "fd_engine_step", "fd_engine_shot_status", "fd_engine_release",
+            "fd_engine_stream", "fd_engine_sync", "fd_engine_destroy")
 
 
 class FdGrid(ctypes.Structure):
@@ -86,6 +88,22 @@ def load(path: str = LIB_PATH):
         lib.fd_set_acoustic_config.restype = I
         lib.fd_num_acoustic_configs.argtypes = [I]
         lib.fd_num_acoustic_configs.restype = I
+        VP = ctypes.POINTER(ctypes.c_void_p)
+        L64 = ctypes.POINTER(ctypes.c_int64)
+        IP = ctypes.POINTER(ctypes.c_int)
+        lib.fd_engine_footprint.argtypes = [G, I, I, I, L64]
+        lib.fd_engine_create.argtypes = [G, I, D, P, P, I, I, I, VP]
+        lib.fd_engine_add_shot.argtypes = [P, I, I, P, P, I, P, P, IP]
+        lib.fd_engine_step.argtypes = [P, I]
+        lib.fd_engine_shot_status.argtypes = [P, I, IP, L64]
+        lib.fd_engine_release.argtypes = [P, I]
+        lib.fd_engine_stream.argtypes = [P, VP]
+        lib.fd_engine_sync.argtypes = [P]
+        lib.fd_engine_destroy.argtypes = [P]
+        for name in ("fd_engine_footprint", "fd_engine_create", "fd_engine_add_shot",
+                     "fd_engine_step", "fd_engine_shot_status", "fd_engine_release",
+                     "fd_engine_stream", "fd_engine_sync", "fd_engine_destroy"):
+            getattr(lib, name).restype = I
         lib.fd_launch_count.argtypes = []
         lib.fd_launch_count.restype = ctypes.c_int64
         _lib = lib

@@ -125,8 +125,9 @@ __global__ void __launch_bounds__(TX *TY)
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int tx = tid % TX, ty = tid / TX;
-    const int shot = blockIdx.z / nzc;
-    const int chunk = blockIdx.z - shot * nzc;
+    const int shot_i = blockIdx.z / nzc;
+    const int chunk = blockIdx.z - shot_i * nzc;
+    const int shot = a.slot_map ? a.slot_map[shot_i] : shot_i;
     const int x0 = blockIdx.x * C::BX, y0 = blockIdx.y * C::BY;
     const int za = chunk * zchunk;
     const int zb = min(a.L.nz, za + zchunk);
@@ -400,7 +401,8 @@ int acoustic_default_config(int radius) {
 }
 
 fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots, int lps,
-                        float *wave, const float *bcoef, AcousticPlan *plan) {
+                        float *wave, const float *bcoef, AcousticPlan *plan, int map_shots) {
+    if (map_shots < nshots) map_shots = nshots;
     int n = 0;
     const ConfigEntry *tab = config_table(radius, &n);
     if (!tab) return set_error(FD_ERR_SO, "no acoustic kernel for radius %d", radius);
@@ -442,10 +444,10 @@ fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots,
     if (plan->smem > e.smem)
         FD_CUDA_TRY(cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)plan->smem));
-    FD_TRY(make_tensor_map_4d(&plan->map_halo, wave, L.nx, L.ny, L.nz, (uint64_t)nshots * lps,
+    FD_TRY(make_tensor_map_4d(&plan->map_halo, wave, L.nx, L.ny, L.nz, (uint64_t)map_shots * lps,
                               (uint64_t)L.nxp * 4, (uint64_t)L.plane * 4, (uint64_t)L.vol * 4,
                               e.pw, e.ph, 1, 1));
-    FD_TRY(make_tensor_map_4d(&plan->map_int, wave, L.nx, L.ny, L.nz, (uint64_t)nshots * lps,
+    FD_TRY(make_tensor_map_4d(&plan->map_int, wave, L.nx, L.ny, L.nz, (uint64_t)map_shots * lps,
                               (uint64_t)L.nxp * 4, (uint64_t)L.plane * 4, (uint64_t)L.vol * 4,
                               e.bx, e.by, 1, 1));
     return make_tensor_map_4d(&plan->map_b, bcoef, L.nx, L.ny, L.nz, 1, (uint64_t)L.nxp * 4,

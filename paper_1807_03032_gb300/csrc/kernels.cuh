@@ -44,6 +44,9 @@ struct AcousticStepArgs {
     // u^{n-1} from lev_prev, u^{n+1} written to lev_out (== lev_prev for the
     // in-place two-level scheme; distinct when a history is being kept).
     int lps, lev_cur, lev_prev, lev_out;
+    // Optional map from blockIdx.z's shot index to the shot (slot) actually
+    // stepped, so that a batch engine can step only its active slots.
+    const int *slot_map;
     float wc;             // sum over axes of w_0 / h_d^2
     float wx[kMaxRadius + 1], wy[kMaxRadius + 1], wz[kMaxRadius + 1];  // w_k / h_d^2
     unsigned int *err;
@@ -71,9 +74,11 @@ inline void set_two_levels(AcousticStepArgs &a, int cur) {
 
 int acoustic_num_configs(int radius);
 int acoustic_default_config(int radius);
-// `lps` levels per shot are addressable (buffers nshots * lps).
+// `lps` levels per shot are addressable (buffers nshots * lps).  The launch
+// covers `nshots` shots; the tensor maps cover `map_shots` shots (default:
+// nshots) for callers that map launch shots to slots (slot_map).
 fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots, int lps,
-                        float *wave, const float *bcoef, AcousticPlan *plan);
+                        float *wave, const float *bcoef, AcousticPlan *plan, int map_shots = 0);
 fd_status acoustic_launch(const AcousticPlan &plan, const AcousticStepArgs &args,
                           cudaStream_t stream);
 
