@@ -327,6 +327,12 @@ def run_ours(args):
         torch.cuda.empty_cache()
         fwi = run_fwi(args, fd, dev, stream)
 
+    # ---------------------------------------------------------------- serving
+    serving = None
+    if not args.no_serving and "8" in per_so:
+        torch.cuda.empty_cache()
+        serving = run_serving(args, fd, dev, per_so["8"]["kernel_gpts"])
+
     # ---------------------------------------------------------------- CPU baseline (oracle)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -353,6 +359,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "tti": tti,
             "fwi_gradient": fwi,
+            "serving": serving,
             "clocks": clocks,
             "gpu_launches": int(launches),
         }
@@ -450,6 +457,85 @@ def run_fwi(args, fd, dev, stream):
                     "an adjoint sweep"}
 
 
+def serving_jobs(fd, dev, rate_jobs_per_s, n_jobs, seed=6, sizes=(128, 256, 384), h=20.0,
+                 nt_range=(500, 3000), shots_range=(1, 32), so=8, nbl=20):
+    """Served shot stream: Poisson arrivals (seeded) of jobs on one model per
+    grid size in {128^3, 256^3, 384^3} (uniform), nt ~ U{500..3000},
+    1..32 shots per job, so = 8, 128 x 128 receivers at a stride of N/128."""
+    import torch
+    from paper_1807_03032_gb300.serving import Job, Model, Shot
+    rng = np.random.default_rng(seed)
+    models = {}
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    for i, n in enumerate(sizes):
+        shape = (n, n, n)
+        v = workloads.two_layer_velocity(shape, 1.5, 3.0 + 0.25 * i, interface=n // 2)
+        dt = workloads.cfl_dt((h, h, h), 3.0 + 0.25 * i)
+        models[n] = Model(i, fd.Grid(shape, (h, h, h)), so, dt,
+                          T(workloads.slowness_squared(v)),
+                          T(workloads.damping_profile(shape, nbl, (h, h, h), 3.0 + 0.25 * i)))
+    jobs, t = [], 0.0
+    for j in range(n_jobs):
+        t += rng.exponential(1.0 / rate_jobs_per_s)
+        n = int(rng.choice(sizes))
+        md = models[n]
+        stride = n // 128
+        gy, gx = np.meshgrid(np.arange(0, n, stride) * h, np.arange(0, n, stride) * h,
+                             indexing="ij")
+        rec = np.stack([gx.ravel(), gy.ravel(), np.full(gx.size, nbl * h + 0.5 * h)], -1)
+        rec_t = T(rec.astype(np.float32))
+        shots = []
+        for _ in range(int(rng.integers(shots_range[0], shots_range[1] + 1))):
+            nt = int(rng.integers(nt_range[0], nt_range[1] + 1))
+            src = np.array([[rng.uniform(nbl, n - 1 - nbl) * h, rng.uniform(nbl, n - 1 - nbl) * h,
+                             nbl * h + 20.0]], np.float32)
+            wav = workloads.ricker(nt, md.dt)[:, None].astype(np.float32)
+            shots.append(Shot(nt, T(src), T(wav), rec_t))
+        jobs.append(Job(j, md, shots, t))
+    return jobs
+
+
+def run_serving(args, fd, dev, gpts_so8):
+    """Continuous-batching server vs one acoustic_forward call per shot, same
+    arrivals; rate = 0.8 x the capacity implied by the measured so-8 kernel
+    throughput of this run."""
+    import torch
+    from paper_1807_03032_gb300.serving import Server, latency_stats, one_shot_per_launch
+    sizes = (128, 256, 384)
+    mean_pts = np.mean([n ** 3 for n in sizes]) * 1750.0 * 16.5
+    capacity = gpts_so8 * 1e9 / mean_pts
+    rate = 0.8 * capacity
+    jobs = serving_jobs(fd, dev, rate, args.serve_jobs)
+    nshots = sum(len(j.shots) for j in jobs)
+    pts = sum(j.model.grid.shape[0] ** 3 * (s.nt - 1) for j in jobs for s in j.shots)
+    srv = Server(hbm_budget=int(args.serve_budget_gb * (1 << 30)), max_slots=32, chunk=32,
+                 max_nsrc=1, max_nrec=128 * 128)
+    t0 = time.perf_counter()
+    srv.run(jobs)
+    make = time.perf_counter() - t0
+    srv.close()
+    served = {"shots_per_s": round(nshots / make, 3), "gpts": round(pts / make / 1e9, 2),
+              "makespan_s": round(make, 2), **{k: round(v, 3) for k, v in latency_stats(jobs).items()},
+              "max_concurrent_shots": srv.max_concurrent_shots,
+              "peak_engine_bytes": srv.peak_used}
+    for j in jobs:
+        for s in j.shots:
+            s.traces = None
+        j.done_at = None
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    one_shot_per_launch(jobs)
+    make_b = time.perf_counter() - t0
+    base = {"shots_per_s": round(nshots / make_b, 3), "gpts": round(pts / make_b / 1e9, 2),
+            "makespan_s": round(make_b, 2), **{k: round(v, 3) for k, v in latency_stats(jobs).items()}}
+    return {"workload": f"{len(jobs)} jobs / {nshots} shots, Poisson arrivals at "
+                        f"{rate:.3f} jobs/s (0.8 x capacity {capacity:.3f} from the so-8 kernel "
+                        f"rate {gpts_so8:.0f} GPts/s), grids {{128,256,384}}^3, nt U{{500..3000}}, "
+                        f"1-32 shots per job, so 8, 128x128 receivers",
+            "batched": served, "one_shot_per_launch": base,
+            "latency_is": "job arrival to delivery of its last shot's traces (device)"}
+
+
 def cpu_baseline(w, so_list):
     """The FP64 oracle, as it stands, on the host cores: one time step of the
     512^3 workload at each space order (a bounded sample of the workload)."""
@@ -522,6 +608,9 @@ def main():
     ap.add_argument("--no-tti", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fwi", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-jobs", type=int, default=10)
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--fwi-n", type=int, default=256)
     ap.add_argument("--fwi-nt", type=int, default=2000)
     args = ap.parse_args()
