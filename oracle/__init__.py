@@ -81,19 +81,26 @@ def _load():
             lib.ora_fd_weights.restype = None
             lib.ora_laplacian.argtypes = [G, I, I, P, P]
             lib.ora_first_derivative.argtypes = [G, I, I, I, P, P]
+            lib.ora_first_derivative_kind.argtypes = [G, I, I, I, I, P, P]
+            lib.ora_staggered_weights.argtypes = [I, P]
+            lib.ora_staggered_weights.restype = None
             lib.ora_acoustic_step.argtypes = [G, I, I, D, P, P, P, P, P]
             lib.ora_interpolate.argtypes = [G, I, P, P, P]
             lib.ora_inject.argtypes = [G, I, P, P, P, P]
             lib.ora_acoustic_forward.argtypes = [G, I, I, D, I, I, P, P, I, P, P, I, P, P, P, P]
             lib.ora_tti_operators.argtypes = [G, I, I, P, P, P, P, P]
+            lib.ora_tti_operators_kind.argtypes = [G, I, I, I, P, P, P, P, P]
             lib.ora_tti_forward.argtypes = [G, I, I, D, I, I, P, P, P, P, P, P,
                                             I, P, P, I, P, P, P, P, P, P]
+            lib.ora_tti_forward_opts.argtypes = [G, I, I, I, I, D, I, I, P, P, P, P, P, P,
+                                                 I, P, P, I, P, P, P, P, P, P]
             lib.ora_acoustic_adjoint.argtypes = [G, I, I, D, I, I, P, P, I, P, P, I, P, P]
             lib.ora_acoustic_gradient.argtypes = [G, I, D, I, I, P, P, I, P, P, I, P, P, P]
             for name in ("ora_acoustic_adjoint", "ora_acoustic_gradient",
                          "ora_laplacian", "ora_first_derivative", "ora_acoustic_step",
                          "ora_interpolate", "ora_inject", "ora_acoustic_forward",
-                         "ora_tti_operators", "ora_tti_forward"):
+                         "ora_tti_operators", "ora_tti_forward", "ora_first_derivative_kind",
+                         "ora_tti_operators_kind", "ora_tti_forward_opts"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -137,12 +144,30 @@ def laplacian(grid: Grid, so: int, u, periodic: bool = False):
     return out
 
 
-def first_derivative(grid: Grid, so: int, axis: int, f, periodic: bool = False):
-    """axis 0 = x, 1 = y, 2 = z (arrays are [z][y][x])."""
+def staggered_weights(r: int):
+    """Staggered first-derivative weights [0, a_1..a_r] for radius r."""
+    a = np.zeros(r + 1)
+    _load().ora_staggered_weights(int(r), _ptr(a))
+    return a
+
+
+_KINDS = {"central": 0, "forward": 1, "backward": -1}
+
+
+def first_derivative(grid: Grid, so: int, axis: int, f, periodic: bool = False,
+                     kind: str = "central"):
+    """axis 0 = x, 1 = y, 2 = z (arrays are [z][y][x]).  kind: "central",
+    "forward" (staggered D+, value at i + 1/2) or "backward" (D-, at i - 1/2)."""
     f = _f64(f)
     out = np.empty_like(f)
-    _check(_load().ora_first_derivative(ctypes.byref(grid), so, int(periodic), axis, _ptr(f),
-                                        _ptr(out)), "first_derivative")
+    lib = _load()
+    if kind == "central":
+        st = lib.ora_first_derivative(ctypes.byref(grid), so, int(periodic), axis, _ptr(f),
+                                      _ptr(out))
+    else:
+        st = lib.ora_first_derivative_kind(ctypes.byref(grid), so, int(periodic), axis,
+                                           _KINDS[kind], _ptr(f), _ptr(out))
+    _check(st, "first_derivative")
     return out
 
 
@@ -202,19 +227,32 @@ def acoustic_forward(grid: Grid, so: int, dt: float, nt: int, m, src_xyz, src_wa
     return rec, ufin
 
 
-def tti_operators(grid: Grid, so: int, theta, phi, q, periodic: bool = False):
-    """(Hz q, L q) for the rotated TTI operators."""
+_DERIVS = {"centred": 0, "staggered": 1}
+_RECEIVERS = {"p": 0, "mean": 1}
+
+
+def tti_operators(grid: Grid, so: int, theta, phi, q, periodic: bool = False,
+                  deriv: str = "centred"):
+    """(Hz q, L q) for the rotated TTI operators (deriv "centred" or "staggered")."""
     theta, phi, q = _f64(theta), _f64(phi), _f64(q)
     hz = np.empty_like(q)
     lq = np.empty_like(q)
-    _check(_load().ora_tti_operators(ctypes.byref(grid), so, int(periodic), _ptr(theta),
-                                     _ptr(phi), _ptr(q), _ptr(hz), _ptr(lq)), "tti_operators")
+    lib = _load()
+    if deriv == "centred":
+        st = lib.ora_tti_operators(ctypes.byref(grid), so, int(periodic), _ptr(theta),
+                                   _ptr(phi), _ptr(q), _ptr(hz), _ptr(lq))
+    else:
+        st = lib.ora_tti_operators_kind(ctypes.byref(grid), so, int(periodic), _DERIVS[deriv],
+                                        _ptr(theta), _ptr(phi), _ptr(q), _ptr(hz), _ptr(lq))
+    _check(st, "tti_operators")
     return hz, lq
 
 
 def tti_forward(grid: Grid, so: int, dt: float, nt: int, m, eps, delta, theta, phi, src_xyz,
-                src_wav, rec_xyz, damp=None, p_init=None, r_init=None, periodic: bool = False):
-    """Full TTI forward run.  Returns (rec, p_final, r_final) in FP64."""
+                src_wav, rec_xyz, damp=None, p_init=None, r_init=None, periodic: bool = False,
+                deriv: str = "centred", receiver: str = "p"):
+    """Full TTI forward run.  Returns (rec, p_final, r_final) in FP64.
+    deriv: "centred" or "staggered"; receiver: "p" or "mean" ((p + r)/2)."""
     m, eps, delta, theta, phi = (_f32(a) for a in (m, eps, delta, theta, phi))
     damp = _f32(damp)
     src_xyz, src_wav, rec_xyz = _f32(src_xyz), _f32(src_wav), _f32(rec_xyz)
@@ -224,11 +262,20 @@ def tti_forward(grid: Grid, so: int, dt: float, nt: int, m, eps, delta, theta, p
     rec = np.zeros((nshots, nt, nrec))
     pfin = np.zeros((nshots, 2) + m.shape)
     rfin = np.zeros((nshots, 2) + m.shape)
-    st = _load().ora_tti_forward(ctypes.byref(grid), so, int(periodic), float(dt), int(nt),
+    lib = _load()
+    if deriv == "centred" and receiver == "p":
+        st = lib.ora_tti_forward(ctypes.byref(grid), so, int(periodic), float(dt), int(nt),
                                  nshots, _ptr(m), _ptr(damp), _ptr(eps), _ptr(delta), _ptr(theta),
                                  _ptr(phi), nsrc, _ptr(src_xyz), _ptr(src_wav), nrec,
                                  _ptr(rec_xyz), _ptr(rec), _ptr(p_init), _ptr(r_init),
                                  _ptr(pfin), _ptr(rfin))
+    else:
+        st = lib.ora_tti_forward_opts(ctypes.byref(grid), so, int(periodic), _DERIVS[deriv],
+                                      _RECEIVERS[receiver], float(dt), int(nt), nshots, _ptr(m),
+                                      _ptr(damp), _ptr(eps), _ptr(delta), _ptr(theta), _ptr(phi),
+                                      nsrc, _ptr(src_xyz), _ptr(src_wav), nrec, _ptr(rec_xyz),
+                                      _ptr(rec), _ptr(p_init), _ptr(r_init), _ptr(pfin),
+                                      _ptr(rfin))
     _check(st, "tti_forward")
     return rec, pfin, rfin
 

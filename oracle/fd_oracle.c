@@ -44,6 +44,9 @@
  *       m p_tt + damp p_t = (1+2 eps) Hxy p + sqrt(1+2 delta) Hz r,
  *       m r_tt + damp r_t = sqrt(1+2 delta) Hxy p + Hz r;
  *     the source is injected into p and r, receivers record p.
+ *     Alternative readings (selectable, defaults as above): staggered first
+ *     derivatives (inner D+, outer D-, each the other's negative transpose)
+ *     and receivers recording (p + r)/2.
  *
  * Layout: C order [z][y][x] (x fastest), index (k*ny + j)*nx + i.
  */
@@ -104,6 +107,29 @@ void ora_fd_weights(int r, double *w, double *c) {
     w[0] = -2.0 * sum;
 }
 
+/* Staggered first-derivative weights for radius r (order 2r): the derivative
+ * at a point midway between nodes, from the r node pairs at distances
+ * (k - 1/2) h on either side,
+ *   f'(x) ~ sum_k a[k] (f(x + (k - 1/2) h) - f(x - (k - 1/2) h)) / h,
+ * closed form a[k] = (-1)^(k+1) ((2r-1)!!)^2 / (4^(r-1) (2k-1)^2 (r+k-1)! (r-k)!).
+ * For r = 1 this is a[1] = 1 (the two-point difference), r = 2 gives 9/8, -1/24.
+ * Used by the staggered reading of the rotated TTI operators. */
+void ora_staggered_weights(int r, double *a) {
+    double dfact = 1.0; /* (2r-1)!! */
+    for (int j = 1; j <= 2 * r - 1; j += 2) dfact *= (double)j;
+    double p4 = 1.0; /* 4^(r-1) */
+    for (int j = 1; j < r; ++j) p4 *= 4.0;
+    a[0] = 0.0;
+    for (int k = 1; k <= r; ++k) {
+        double f1 = 1.0, f2 = 1.0; /* (r+k-1)!, (r-k)! */
+        for (int j = 2; j <= r + k - 1; ++j) f1 *= (double)j;
+        for (int j = 2; j <= r - k; ++j) f2 *= (double)j;
+        double sgn = (k % 2 == 1) ? 1.0 : -1.0;
+        double odd = (double)(2 * k - 1);
+        a[k] = sgn * dfact * dfact / (p4 * odd * odd * f1 * f2);
+    }
+}
+
 static int radius_of(int so) {
     if (so < 2 || so > 32 || (so % 2) != 0) return -1;
     return so / 2;
@@ -132,26 +158,44 @@ int ora_laplacian(const ora_grid *g, int so, int periodic, const double *u, doub
     return ORA_OK;
 }
 
-/* Central first derivative along one axis (0 = x, 1 = y, 2 = z). */
-int ora_first_derivative(const ora_grid *g, int so, int periodic, int axis, const double *f,
-                         double *out) {
+/* First derivative along one axis (0 = x, 1 = y, 2 = z) of one of three kinds:
+ *   kind  0: central, at the node:     sum_k c_k (f[i+k] - f[i-k]) / h;
+ *   kind +1: forward-staggered D+, the derivative at i + 1/2:
+ *                                      sum_k a_k (f[i+k] - f[i-k+1]) / h;
+ *   kind -1: backward-staggered D-, the derivative at i - 1/2:
+ *                                      sum_k a_k (f[i+k-1] - f[i-k]) / h.
+ * With zero ghosts (or periodic images) D- = -(D+)^T exactly. */
+int ora_first_derivative_kind(const ora_grid *g, int so, int periodic, int axis, int kind,
+                              const double *f, double *out) {
     int r = radius_of(so);
-    if (r < 0 || axis < 0 || axis > 2) return ORA_ERR_ARG;
-    double w[33], c[33];
+    if (r < 0 || axis < 0 || axis > 2 || kind < -1 || kind > 1) return ORA_ERR_ARG;
+    double w[33], c[33], a[33];
     ora_fd_weights(r, w, c);
+    ora_staggered_weights(r, a);
     const int di = axis == 0, dj = axis == 1, dk = axis == 2;
     const double h = axis == 0 ? g->hx : (axis == 1 ? g->hy : g->hz);
+    /* taps (offset of the "+" node, offset of the "-" node) for pair s */
+    const int plus0 = kind == -1 ? -1 : 0, minus0 = kind == 1 ? 1 : 0;
 #pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < g->nz; ++k)
         for (int j = 0; j < g->ny; ++j)
             for (int i = 0; i < g->nx; ++i) {
                 double d = 0.0;
-                for (int s = 1; s <= r; ++s)
-                    d += c[s] * (at(g, periodic, f, i + s * di, j + s * dj, k + s * dk) -
-                                 at(g, periodic, f, i - s * di, j - s * dj, k - s * dk));
+                for (int s = 1; s <= r; ++s) {
+                    const int sp = s + plus0, sm = -s + minus0;
+                    d += (kind == 0 ? c[s] : a[s]) *
+                         (at(g, periodic, f, i + sp * di, j + sp * dj, k + sp * dk) -
+                          at(g, periodic, f, i + sm * di, j + sm * dj, k + sm * dk));
+                }
                 out[lin(g, i, j, k)] = d / h;
             }
     return ORA_OK;
+}
+
+/* Central first derivative along one axis (0 = x, 1 = y, 2 = z). */
+int ora_first_derivative(const ora_grid *g, int so, int periodic, int axis, const double *f,
+                         double *out) {
+    return ora_first_derivative_kind(g, so, periodic, axis, 0, f, out);
 }
 
 /* damp(i,j,k) from the per-axis 1-D profiles (NULL = no damping). */
@@ -344,12 +388,19 @@ done:
 /*
  * TTI operators for one field q: Hz q = sum_i D_i(n_i (n . grad q)) and
  * L q = sum_i D_i D_i q, with n = (sin t cos f, sin t sin f, cos t) per point.
- * D is the central first derivative of order so; temporaries outside the
- * grid are zero ghosts (or periodic images).  Evaluated literally: gradient,
- * projection on n, scaling by n_i, second first-derivative pass.
+ * deriv = 0: D is the central first derivative of order so (inner and outer);
+ * deriv = 1: the staggered reading, inner derivatives D+ and outer D-
+ *   Hz q = sum_i D-_i(n_i sum_j n_j D+_j q),  L q = sum_i D-_i D+_i q,
+ * with n sampled at the nodes (the half-point shifts are not interpolated).
+ * Temporaries outside the grid are zero ghosts (or periodic images).
+ * Evaluated literally: gradient, projection on n, scaling by n_i, second
+ * first-derivative pass.
  */
-int ora_tti_operators(const ora_grid *g, int so, int periodic, const double *theta,
-                      const double *phi, const double *q, double *hz, double *lq) {
+int ora_tti_operators_kind(const ora_grid *g, int so, int periodic, int deriv,
+                           const double *theta, const double *phi, const double *q, double *hz,
+                           double *lq) {
+    if (deriv < 0 || deriv > 1) return ORA_ERR_ARG;
+    const int inner = deriv ? 1 : 0, outer = deriv ? -1 : 0;
     const size_t N = npts(g);
     double *grad[3], *proj, *tmp, *dtmp;
     int st = ORA_OK;
@@ -363,7 +414,7 @@ int ora_tti_operators(const ora_grid *g, int so, int periodic, const double *the
     }
     /* gradient of q */
     for (int a = 0; a < 3; ++a) {
-        st = ora_first_derivative(g, so, periodic, a, q, grad[a]);
+        st = ora_first_derivative_kind(g, so, periodic, a, inner, q, grad[a]);
         if (st) goto done;
     }
     /* projection on the symmetry axis: proj = n . grad q */
@@ -383,12 +434,12 @@ int ora_tti_operators(const ora_grid *g, int so, int periodic, const double *the
                                      : cos(theta[p]);
                 tmp[p] = na * proj[p];
             }
-            ora_first_derivative(g, so, periodic, a, tmp, dtmp);
+            ora_first_derivative_kind(g, so, periodic, a, outer, tmp, dtmp);
             for (size_t p = 0; p < N; ++p) hz[p] += dtmp[p];
         }
         if (lq) {
             /* lq += D_a (D_a q) */
-            ora_first_derivative(g, so, periodic, a, grad[a], dtmp);
+            ora_first_derivative_kind(g, so, periodic, a, outer, grad[a], dtmp);
             for (size_t p = 0; p < N; ++p) lq[p] += dtmp[p];
         }
     }
@@ -400,23 +451,46 @@ done:
     return st;
 }
 
+int ora_tti_operators(const ora_grid *g, int so, int periodic, const double *theta,
+                      const double *phi, const double *q, double *hz, double *lq) {
+    return ora_tti_operators_kind(g, so, periodic, 0, theta, phi, q, hz, lq);
+}
+
+/* TTI receivers: interp(p), or interp((p + r)/2) with receiver = 1 (tmp is
+ * scratch of one field). */
+static void record(const ora_grid *g, int receiver, int nrec, const float *rxyz,
+                   const double *p, const double *r, double *tmp, double *out) {
+    if (!receiver) {
+        ora_interpolate(g, nrec, rxyz, p, out);
+        return;
+    }
+    const size_t N = npts(g);
+    for (size_t i = 0; i < N; ++i) tmp[i] = 0.5 * (p[i] + r[i]);
+    ora_interpolate(g, nrec, rxyz, tmp, out);
+}
+
 /*
  * TTI forward model (two coupled fields p, r).  Per shot and step n:
  *   Hxy p = L p - Hz p;
  *   m p_tt + damp p_t = (1+2 eps) Hxy p + sqrt(1+2 delta) Hz r
  *   m r_tt + damp r_t = sqrt(1+2 delta) Hxy p + Hz r
  * each advanced with the same centred leapfrog as the acoustic case; src[n]
- * is injected into p^{n+1} and r^{n+1}; rec[n] = interp(p^n).
+ * is injected into p^{n+1} and r^{n+1}; rec[n] = interp(p^n), or with
+ * receiver = 1 the alternative reading rec[n] = interp((p^n + r^n) / 2).
+ * deriv selects the central (0) or staggered (1) first derivatives of
+ * ora_tti_operators_kind.
  * Fields eps, delta, theta, phi are [nz][ny][nx].  p_init/r_init and
  * p_final/r_final are [nshots][2][nz][ny][nx] (levels n, n-1) or NULL.
  */
-int ora_tti_forward(const ora_grid *g, int so, int periodic, double dt, int nt, int nshots,
-                    const float *m32, const float *damp32, const float *eps32,
-                    const float *delta32, const float *theta32, const float *phi32, int nsrc,
-                    const float *src_xyz, const float *src_wav, int nrec, const float *rec_xyz,
-                    double *rec_out, const float *p_init, const float *r_init, double *p_final,
-                    double *r_final) {
+int ora_tti_forward_opts(const ora_grid *g, int so, int periodic, int deriv, int receiver,
+                         double dt, int nt, int nshots, const float *m32, const float *damp32,
+                         const float *eps32, const float *delta32, const float *theta32,
+                         const float *phi32, int nsrc, const float *src_xyz,
+                         const float *src_wav, int nrec, const float *rec_xyz, double *rec_out,
+                         const float *p_init, const float *r_init, double *p_final,
+                         double *r_final) {
     if (radius_of(so) < 0 || nt < 1 || nshots < 1 || nsrc < 0 || nrec < 0) return ORA_ERR_ARG;
+    if (deriv < 0 || deriv > 1 || receiver < 0 || receiver > 1) return ORA_ERR_ARG;
     const size_t N = npts(g);
     for (int s = 0; s < nshots; ++s) {
         if (check_sparse(g, nsrc, src_xyz + (size_t)s * nsrc * 3)) return ORA_ERR_COORD;
@@ -450,8 +524,8 @@ int ora_tti_forward(const ora_grid *g, int so, int periodic, double dt, int nt, 
             rm[i] = r_init ? (double)r_init[((size_t)s * 2 + 1) * N + i] : 0.0;
         }
         for (int n = 0; n + 1 < nt; ++n) {
-            st = ora_tti_operators(g, so, periodic, th, ph, p, hzp, lp);
-            if (!st) st = ora_tti_operators(g, so, periodic, th, ph, r, hzr, NULL);
+            st = ora_tti_operators_kind(g, so, periodic, deriv, th, ph, p, hzp, lp);
+            if (!st) st = ora_tti_operators_kind(g, so, periodic, deriv, th, ph, r, hzr, NULL);
             if (st) goto done;
             /* p equation: rhs = (1+2eps)(Lp - Hz p) + sqrt(1+2delta) Hz r */
             for (size_t i = 0; i < N; ++i)
@@ -464,7 +538,7 @@ int ora_tti_forward(const ora_grid *g, int so, int periodic, double dt, int nt, 
             for (int k = 0; k < nsrc; ++k) q[k] = (double)src_wav[((size_t)s * nt + n) * nsrc + k];
             ora_inject(g, nsrc, sxyz, q, scale, pn);
             ora_inject(g, nsrc, sxyz, q, scale, rn);
-            if (rec) ora_interpolate(g, nrec, rxyz, p, rec + (size_t)n * nrec);
+            if (rec) record(g, receiver, nrec, rxyz, p, r, rhs, rec + (size_t)n * nrec);
             double *t = pm;
             pm = p;
             p = pn;
@@ -474,7 +548,7 @@ int ora_tti_forward(const ora_grid *g, int so, int periodic, double dt, int nt, 
             r = rn;
             rn = t;
         }
-        if (rec) ora_interpolate(g, nrec, rxyz, p, rec + (size_t)(nt - 1) * nrec);
+        if (rec) record(g, receiver, nrec, rxyz, p, r, rhs, rec + (size_t)(nt - 1) * nrec);
         if (p_final) {
             memcpy(p_final + ((size_t)s * 2 + 0) * N, p, N * sizeof(double));
             memcpy(p_final + ((size_t)s * 2 + 1) * N, pm, N * sizeof(double));
@@ -495,6 +569,17 @@ done:
     free(q);
     for (int b = 0; b < 10; ++b) free(bufs[b]);
     return st;
+}
+
+int ora_tti_forward(const ora_grid *g, int so, int periodic, double dt, int nt, int nshots,
+                    const float *m32, const float *damp32, const float *eps32,
+                    const float *delta32, const float *theta32, const float *phi32, int nsrc,
+                    const float *src_xyz, const float *src_wav, int nrec, const float *rec_xyz,
+                    double *rec_out, const float *p_init, const float *r_init, double *p_final,
+                    double *r_final) {
+    return ora_tti_forward_opts(g, so, periodic, 0, 0, dt, nt, nshots, m32, damp32, eps32,
+                                delta32, theta32, phi32, nsrc, src_xyz, src_wav, nrec, rec_xyz,
+                                rec_out, p_init, r_init, p_final, r_final);
 }
 
 /* ------------------------------------------------------------------------- */

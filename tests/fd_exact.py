@@ -55,3 +55,22 @@ def first_symbol(r, theta):
     """s(theta) with  D1 e^{i k x} = i s(k h)/h e^{i k x}."""
     c = first_derivative_weights(r)
     return 2.0 * sum(float(c[k]) * math.sin(k * theta) for k in range(1, r + 1))
+
+
+def staggered_weights(r):
+    """[0, a1, ..., ar] with sum_k a_k 2 (k - 1/2)^p = delta_{p,1}, p = 1,3,..,2r-1
+    (first derivative at a half point from nodes at +-(k - 1/2) h)."""
+    rows, rhs = [], []
+    half = Fraction(1, 2)
+    for q in range(r):
+        p = 2 * q + 1
+        rows.append([2 * (k - half) ** p for k in range(1, r + 1)])
+        rhs.append(Fraction(1) if p == 1 else Fraction(0))
+    return [Fraction(0)] + _solve(rows, rhs)
+
+
+def staggered_symbol(r, theta):
+    """s(theta) with  D+ e^{i k x} = e^{i theta/2} i s(theta)/h e^{i k x} and
+    D- e^{i k x} = e^{-i theta/2} i s(theta)/h e^{i k x}, theta = k h."""
+    a = staggered_weights(r)
+    return 2.0 * sum(float(a[k]) * math.sin((k - 0.5) * theta) for k in range(1, r + 1))
