@@ -409,7 +409,53 @@ def run_tti(args, fd, _native, dev, stream, peak):
                                   "pass1_ms": round(p1[0] / max(p1[1], 1), 4),
                                   "pass2_ms": round(p2[0] / max(p2[1], 1), 4),
                                   "hbm_frac_44B": round(gb / peak, 4)}
+    if not args.no_tti_ablation:
+        out["ablation"] = run_tti_ablation(args, fd, _native, g, w, m, e, d, th, ph, sx, sw, rx,
+                                           dd, out["per_so"])
     return out
+
+
+def run_tti_ablation(args, fd, _native, g, w, m, e, d, th, ph, sx, sw, rx, dd, per_so):
+    """TTI variants on the same workload, per-step kernel time over a short
+    run: temporaries (two passes) vs recomputed inner derivatives (one pass),
+    centred vs staggered first derivatives.  FMA counts per point per step
+    are those of the kernel sources (R = so/2): two passes 24R + 30, recompute
+    72R^2 + 60R (the inner gradient of p and r at each of the 6R outer taps)."""
+    import torch
+    nt_ab = 24
+    sw_ab = sw[:, :nt_ab].contiguous()
+    rec = torch.empty((1, nt_ab, rx.shape[1]), dtype=torch.float32, device=sw.device)
+    res = {"steps": nt_ab - 1, "note": "per-step kernel ms from the library's per-launch events; "
+           "two_pass_centred from the main TTI run"}
+    for so in args.so:
+        R = so // 2
+        row = {"two_pass_centred_ms": per_so[str(so)]["step_kernel_ms"],
+               "fma_per_point": {"two_pass": 24 * R + 30, "recompute": 72 * R * R + 60 * R}}
+        for deriv, scheme, key in (("staggered", "two_pass", "two_pass_staggered_ms"),
+                                   ("centred", "recompute", "recompute_centred_ms"),
+                                   ("staggered", "recompute", "recompute_staggered_ms")):
+            fd.tti_forward(g, so, w.dt, 4, m, e, d, th, ph, sx, sw_ab[:, :4].contiguous(), rx,
+                           damp=dd, rec_out=rec[:, :4].contiguous(), return_final=False,
+                           deriv=deriv, scheme=scheme)
+            _native.stats_reset()
+            _native.stats_enable(True)
+            fd.tti_forward(g, so, w.dt, nt_ab, m, e, d, th, ph, sx, sw_ab, rx, damp=dd,
+                           rec_out=rec, return_final=False, deriv=deriv, scheme=scheme)
+            torch.cuda.synchronize()
+            if scheme == "two_pass":
+                p1 = _native.stats_get("tti_pass1")
+                p2 = _native.stats_get("tti_pass2")
+                kms = (p1[0] + p2[0]) / max(p1[1], 1)
+            else:
+                pr = _native.stats_get("tti_recompute")
+                kms = pr[0] / max(pr[1], 1)
+            _native.stats_enable(False)
+            row[key] = round(kms, 4)
+        row["recompute_over_two_pass"] = round(row["recompute_centred_ms"] /
+                                               row["two_pass_centred_ms"], 2)
+        res[str(so)] = row
+        log(f"[bench] TTI ablation so={so}: {row}")
+    return res
 
 
 def run_fwi(args, fd, dev, stream):
@@ -606,6 +652,7 @@ def main():
     ap.add_argument("--so", type=int, nargs="+", default=list(SO_LIST))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tti", action="store_true")
+    ap.add_argument("--no-tti-ablation", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fwi", action="store_true")
     ap.add_argument("--no-serving", action="store_true")

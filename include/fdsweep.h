@@ -131,6 +131,50 @@ fd_status tti_forward(const fd_grid *grid, int so, double dt, int nt, int nshots
                       void *stream);
 
 /*
+ * tti_forward_opts -- tti_forward with the alternative readings and schemes
+ * of the TTI ablation.  The paper builds the TTI Laplacians from "rotated
+ * first derivative operators" (section "Test case setup") without saying
+ * which first derivative, nor which field the receivers record; its
+ * performance section compares operators generated with and without
+ * shift-invariant temporaries (`advanced` vs `aggressive`, Table tti:ops).
+ *
+ *   opts->deriv     FD_TTI_CENTRED: D_i central of order so (tti_forward);
+ *                   FD_TTI_STAGGERED: inner derivatives D+_j (half a node
+ *                   ahead) and outer D-_i (half a node behind), weights
+ *                   a_k = (-1)^(k+1) ((2r-1)!!)^2 / (4^(r-1) (2k-1)^2
+ *                   (r+k-1)! (r-k)!), so that D- = -(D+)^T and
+ *                   L q = sum_i D-_i D+_i q; n stays at the nodes.  The
+ *                   stability bound uses the staggered symbol.
+ *   opts->receiver  FD_TTI_REC_P: receivers record p; FD_TTI_REC_MEAN: they
+ *                   record (p + r)/2.
+ *   opts->scheme    FD_TTI_TWO_PASS: six first-derivative temporaries per
+ *                   point are written once and differentiated again (the
+ *                   default, linear work in so); FD_TTI_RECOMPUTE: no
+ *                   temporaries, the inner derivatives are recomputed at
+ *                   every outer stencil point (work quadratic in so; one
+ *                   kernel per step; uses 6 fewer fields of device memory).
+ *   opts            NULL selects the tti_forward defaults.  Out-of-range
+ *                   values return FD_ERR_ARG.
+ * Other arguments, ownership and errors as for tti_forward.
+ */
+enum { FD_TTI_CENTRED = 0, FD_TTI_STAGGERED = 1 };
+enum { FD_TTI_REC_P = 0, FD_TTI_REC_MEAN = 1 };
+enum { FD_TTI_TWO_PASS = 0, FD_TTI_RECOMPUTE = 1 };
+typedef struct {
+    int32_t deriv;
+    int32_t receiver;
+    int32_t scheme;
+} fd_tti_options;
+
+fd_status tti_forward_opts(const fd_grid *grid, int so, double dt, int nt, int nshots,
+                           const float *m, const float *damp, const float *epsilon,
+                           const float *delta, const float *theta, const float *phi, int nsrc,
+                           const float *src_xyz, const float *src_wav, int nrec,
+                           const float *rec_xyz, float *rec_out, const float *p_init,
+                           const float *r_init, float *p_final, float *r_final,
+                           const fd_tti_options *opts, void *stream);
+
+/*
  * acoustic_adjoint -- adjoint of acoustic_forward's source-to-receiver map.
  *
  * The paper motivates saving the forward wavefield with "data inversion using
@@ -263,7 +307,8 @@ const char *fd_version(void);
  * entry points launch their time loop without CUDA graphs and bracket every
  * stencil-kernel launch with CUDA events on the call's stream; the elapsed
  * times are accumulated per kernel family when the call completes.
- * Families: "acoustic_step", "tti_pass1", "tti_pass2", "sparse".
+ * Families: "acoustic_step", "tti_pass1", "tti_pass2", "tti_recompute" (the
+ * one-kernel TTI scheme of tti_forward_opts), "sparse".
  * fd_stats_get returns FD_ERR_ARG for an unknown family.
  */
 fd_status fd_stats_enable(int on);

@@ -12,6 +12,8 @@ time in ms; velocity in km/s; m = 1/v^2.
 """
 from __future__ import annotations
 
+import ctypes
+
 from dataclasses import dataclass
 
 import numpy as np
@@ -118,8 +120,12 @@ def acoustic_forward(grid, so, dt, nt, m, src_xyz, src_wav, rec_xyz, damp=None, 
 
 def tti_forward(grid, so, dt, nt, m, eps, delta, theta, phi, src_xyz, src_wav, rec_xyz,
                 damp=None, p_init=None, r_init=None, rec_out=None, p_final=None, r_final=None,
-                return_final=True, stream=None):
-    """TTI forward model (C ABI ``tti_forward``).  Returns (rec, p_final, r_final)."""
+                return_final=True, stream=None, deriv="centred", receiver="p",
+                scheme="two_pass"):
+    """TTI forward model (C ABI ``tti_forward``, or ``tti_forward_opts`` for the
+    alternative readings).  deriv: "centred" | "staggered"; receiver: "p" |
+    "mean" ((p + r)/2); scheme: "two_pass" (temporaries) | "recompute".
+    Returns (rec, p_final, r_final)."""
     g = _as_grid(grid)
     nshots, nsrc = int(src_xyz.shape[0]), int(src_xyz.shape[1])
     nrec = int(rec_xyz.shape[1])
@@ -133,12 +139,18 @@ def tti_forward(grid, so, dt, nt, m, eps, delta, theta, phi, src_xyz, src_wav, r
         if r_final is None:
             r_final = _empty_like_kind(m, (nshots, 2) + tuple(g.shape))
     lib = _native.load()
-    st = lib.tti_forward(
-        g.struct(), int(so), float(dt), int(nt), nshots, _ptr(m, "m"), _ptr(damp, "damp"),
-        _ptr(eps, "eps"), _ptr(delta, "delta"), _ptr(theta, "theta"), _ptr(phi, "phi"), nsrc,
-        _ptr(src_xyz, "src_xyz"), _ptr(src_wav, "src_wav"), nrec, _ptr(rec_xyz, "rec_xyz"),
-        _ptr(rec_out, "rec_out"), _ptr(p_init, "p_init"), _ptr(r_init, "r_init"),
-        _ptr(p_final, "p_final"), _ptr(r_final, "r_final"), _stream_for(m, rec_out, stream=stream))
+    args = (g.struct(), int(so), float(dt), int(nt), nshots, _ptr(m, "m"), _ptr(damp, "damp"),
+            _ptr(eps, "eps"), _ptr(delta, "delta"), _ptr(theta, "theta"), _ptr(phi, "phi"),
+            nsrc, _ptr(src_xyz, "src_xyz"), _ptr(src_wav, "src_wav"), nrec,
+            _ptr(rec_xyz, "rec_xyz"), _ptr(rec_out, "rec_out"), _ptr(p_init, "p_init"),
+            _ptr(r_init, "r_init"), _ptr(p_final, "p_final"), _ptr(r_final, "r_final"))
+    stream_ptr = _stream_for(m, rec_out, stream=stream)
+    if (deriv, receiver, scheme) == ("centred", "p", "two_pass"):
+        st = lib.tti_forward(*args, stream_ptr)
+    else:
+        opts = _native.FdTtiOptions(_native.TTI_DERIV[deriv], _native.TTI_RECEIVER[receiver],
+                                    _native.TTI_SCHEME[scheme])
+        st = lib.tti_forward_opts(*args, ctypes.byref(opts), stream_ptr)
     _native.check(st)
     return rec_out, p_final, r_final
 

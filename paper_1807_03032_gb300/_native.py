@@ -22,7 +22,7 @@ STATUS_NAMES = {
 }
 
 # Every symbol include/fdsweep.h declares (checked by the ABI test).
-EXPORTED = ("acoustic_forward", "tti_forward", "fd_last_error", "fd_version",
+EXPORTED = ("acoustic_forward", "tti_forward", "tti_forward_opts", "fd_last_error", "fd_version",
             "fd_stats_enable", "fd_stats_reset", "fd_stats_get", "fd_set_acoustic_config",
             "fd_num_acoustic_configs", "fd_launch_count", "acoustic_forward_noalloc",
             "acoustic_adjoint", "acoustic_gradient", "fd_engine_footprint", "fd_engine_create",
@@ -36,6 +36,18 @@ class FdGrid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("hx", ctypes.c_double), ("hy", ctypes.c_double), ("hz", ctypes.c_double),
                 ("ox", ctypes.c_double), ("oy", ctypes.c_double), ("oz", ctypes.c_double)]
+
+
+class FdTtiOptions(ctypes.Structure):
+    """Mirror of fd_tti_options."""
+
+    _fields_ = [("deriv", ctypes.c_int32), ("receiver", ctypes.c_int32),
+                ("scheme", ctypes.c_int32)]
+
+
+TTI_DERIV = {"centred": 0, "staggered": 1}
+TTI_RECEIVER = {"p": 0, "mean": 1}
+TTI_SCHEME = {"two_pass": 0, "recompute": 1}
 
 
 class FdError(RuntimeError):
@@ -73,6 +85,9 @@ def load(path: str = LIB_PATH):
         lib.tti_forward.argtypes = [G, I, D, I, I, P, P, P, P, P, P, I, P, P, I, P, P, P, P, P,
                                     P, P]
         lib.tti_forward.restype = I
+        lib.tti_forward_opts.argtypes = [G, I, D, I, I, P, P, P, P, P, P, I, P, P, I, P, P, P, P,
+                                         P, P, ctypes.POINTER(FdTtiOptions), P]
+        lib.tti_forward_opts.restype = I
         lib.fd_last_error.argtypes = []
         lib.fd_last_error.restype = ctypes.c_char_p
         lib.fd_version.argtypes = []

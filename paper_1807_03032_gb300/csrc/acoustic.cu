@@ -107,7 +107,10 @@ __device__ __forceinline__ Q4 lds_q4(const float *p) {
     return Q4{t.x, t.y};
 }
 
-template <int R, int TX, int TY, int VY, int D>
+// U: unroll factor of the plane loop.  The pending-output registers shift by
+// one plane per iteration; unrolling by U turns U - 1 of every U shifts into
+// register renaming instead of moves (U = 2R removes them all).
+template <int R, int TX, int TY, int VY, int D, int U>
 __global__ void __launch_bounds__(TX *TY)
     acoustic_step_kernel(const __grid_constant__ CUtensorMap map_halo,
                          const __grid_constant__ CUtensorMap map_int,
@@ -199,6 +202,7 @@ __global__ void __launch_bounds__(TX *TY)
         for (int v = 0; v < VY; ++v) acc[i][v] = Q4{0ull, 0ull};
 
     bool failed = false;
+#pragma unroll U
     for (int j = 0; j < nplanes; ++j) {
         if (tid == 0 && j + D < nplanes && !failed) {
             if (!issue(j + D)) {
@@ -355,34 +359,49 @@ struct ConfigEntry {
     const char *name;
 };
 
-template <int R, int TX, int TY, int VY, int D>
+template <int R, int TX, int TY, int VY, int D, int U>
 ConfigEntry make_entry(const char *name) {
     using C = AcCfg<R, TX, TY, VY, D>;
-    return ConfigEntry{R,       TX,    TY,    VY,    D,         (const void *)&acoustic_step_kernel<R, TX, TY, VY, D>,
+    return ConfigEntry{R,       TX,    TY,    VY,    D,
+                       (const void *)&acoustic_step_kernel<R, TX, TY, VY, D, U>,
                        C::SMEM, C::BX, C::BY, C::PW, C::PH, C::THREADS, name};
 }
 
-#define FD_AC_ENTRY(R, TX, TY, VY, D) \
-    make_entry<R, TX, TY, VY, D>("acoustic_step<" #R "," #TX "," #TY "," #VY "," #D ">")
+#define FD_AC_ENTRY(R, TX, TY, VY, D, U)                                           \
+    make_entry<R, TX, TY, VY, D, U>("acoustic_step<" #R "," #TX "," #TY "," #VY "," #D \
+                                    "," #U ">")
 
 const ConfigEntry *config_table(int radius, int *count) {
     // Index 0 is the default; the others are kept for tuning sweeps
-    // (fd_set_acoustic_config).  Defaults measured on GB300 at 512^3.
-    static const ConfigEntry r1[] = {FD_AC_ENTRY(1, 16, 16, 1, 4)};
-    static const ConfigEntry r2[] = {FD_AC_ENTRY(2, 16, 16, 1, 4), FD_AC_ENTRY(2, 16, 16, 1, 6),
-                                     FD_AC_ENTRY(2, 16, 8, 1, 6), FD_AC_ENTRY(2, 16, 8, 2, 4)};
-    static const ConfigEntry r4[] = {FD_AC_ENTRY(4, 16, 8, 1, 3), FD_AC_ENTRY(4, 16, 8, 1, 5),
-                                     FD_AC_ENTRY(4, 16, 16, 1, 4), FD_AC_ENTRY(4, 16, 8, 2, 3)};
-    static const ConfigEntry r6[] = {FD_AC_ENTRY(6, 16, 8, 1, 2), FD_AC_ENTRY(6, 16, 8, 1, 4),
-                                     FD_AC_ENTRY(6, 16, 16, 1, 3), FD_AC_ENTRY(6, 8, 16, 1, 3)};
-    static const ConfigEntry r8[] = {FD_AC_ENTRY(8, 16, 8, 1, 2), FD_AC_ENTRY(8, 16, 8, 1, 4),
-                                     FD_AC_ENTRY(8, 16, 16, 1, 3), FD_AC_ENTRY(8, 8, 16, 1, 3)};
+    // (fd_set_acoustic_config).  Defaults measured on GB300 at 512^3: the
+    // plane-loop unroll U = 4 gains 2 % at R = 2 and 10 % at R = 6; at R = 4
+    // and R = 8 it gains nothing, and U = 2R costs occupancy (registers).
+    static const ConfigEntry r1[] = {FD_AC_ENTRY(1, 16, 16, 1, 4, 1)};
+    static const ConfigEntry r2[] = {
+        FD_AC_ENTRY(2, 16, 16, 1, 4, 4), FD_AC_ENTRY(2, 16, 16, 1, 6, 1),
+        FD_AC_ENTRY(2, 16, 8, 1, 6, 1),  FD_AC_ENTRY(2, 16, 8, 2, 4, 1),
+        FD_AC_ENTRY(2, 16, 16, 1, 4, 2), FD_AC_ENTRY(2, 16, 16, 1, 4, 1)};
+    static const ConfigEntry r4[] = {
+        FD_AC_ENTRY(4, 16, 8, 1, 3, 1),  FD_AC_ENTRY(4, 16, 8, 1, 5, 1),
+        FD_AC_ENTRY(4, 16, 16, 1, 4, 1), FD_AC_ENTRY(4, 16, 8, 2, 3, 1),
+        FD_AC_ENTRY(4, 16, 8, 1, 3, 2),  FD_AC_ENTRY(4, 16, 8, 1, 3, 4),
+        FD_AC_ENTRY(4, 16, 8, 1, 3, 8)};
+    static const ConfigEntry r6[] = {
+        FD_AC_ENTRY(6, 16, 8, 1, 2, 4),  FD_AC_ENTRY(6, 16, 8, 1, 4, 1),
+        FD_AC_ENTRY(6, 16, 16, 1, 3, 1), FD_AC_ENTRY(6, 8, 16, 1, 3, 1),
+        FD_AC_ENTRY(6, 16, 8, 1, 2, 2),  FD_AC_ENTRY(6, 16, 8, 1, 2, 1),
+        FD_AC_ENTRY(6, 16, 8, 1, 2, 12)};
+    static const ConfigEntry r8[] = {
+        FD_AC_ENTRY(8, 16, 8, 1, 2, 1),  FD_AC_ENTRY(8, 16, 8, 1, 4, 1),
+        FD_AC_ENTRY(8, 16, 16, 1, 3, 1), FD_AC_ENTRY(8, 8, 16, 1, 3, 1),
+        FD_AC_ENTRY(8, 16, 8, 1, 2, 2),  FD_AC_ENTRY(8, 16, 8, 1, 2, 4),
+        FD_AC_ENTRY(8, 16, 8, 1, 2, 16)};
     switch (radius) {
         case 1: *count = 1; return r1;
-        case 2: *count = 4; return r2;
-        case 4: *count = 4; return r4;
-        case 6: *count = 4; return r6;
-        case 8: *count = 4; return r8;
+        case 2: *count = 6; return r2;
+        case 4: *count = 7; return r4;
+        case 6: *count = 7; return r6;
+        case 8: *count = 7; return r8;
         default: *count = 0; return nullptr;
     }
 }

@@ -66,6 +66,33 @@ double first_symbol_sq_max(int r, const double *c) {
     return best;
 }
 
+// Staggered first-derivative weights a_k (k = 1..r) for the derivative midway
+// between nodes from the node pairs at +-(k - 1/2) h:
+//   a_k = (-1)^(k+1) ((2r-1)!!)^2 / (4^(r-1) (2k-1)^2 (r+k-1)! (r-k)!),
+// built as a running product from a_1 (a_{k+1}/a_k = -(2k-1)^2 (r-k) /
+// ((2k+1)^2 (r+k))).
+void staggered_weights(int r, double *a) {
+    double a1 = 1.0;  // ((2r-1)!!)^2 / (4^(r-1) r! (r-1)!)
+    for (int j = 1; j < r; ++j) a1 *= (double)((2 * j + 1) * (2 * j + 1)) / (4.0 * j * (j + 1));
+    a[0] = 0.0;
+    a[1] = a1;
+    for (int k = 1; k < r; ++k)
+        a[k + 1] = -a[k] * (double)((2 * k - 1) * (2 * k - 1)) * (r - k) /
+                   ((double)((2 * k + 1) * (2 * k + 1)) * (r + k));
+}
+
+// max over theta of the squared staggered symbol (2 sum a_k sin((k - 1/2) theta))^2
+double staggered_symbol_sq_max(int r, const double *a) {
+    double best = 0.0;
+    for (int t = 0; t <= 4096; ++t) {
+        const double th = M_PI * t / 4096.0;
+        double s = 0.0;
+        for (int k = 1; k <= r; ++k) s += 2.0 * a[k] * sin((k - 0.5) * th);
+        if (s * s > best) best = s * s;
+    }
+    return best;
+}
+
 bool valid_so(int so) { return so == 2 || so == 4 || so == 8 || so == 12 || so == 16; }
 
 int g_acoustic_config[kMaxRadius + 1] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
@@ -451,11 +478,20 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
                                   int nsrc, const float *src_xyz, const float *src_wav, int nrec,
                                   const float *rec_xyz, float *rec_out, const float *p_init,
                                   const float *r_init, float *p_final, float *r_final,
-                                  cudaStream_t caller) {
+                                  const fd_tti_options *opts, cudaStream_t caller) {
     FD_TRY(validate_common(grid, so, dt, nt, nshots, m, nsrc, src_xyz, src_wav, nrec, rec_xyz,
                            rec_out));
     if (!eps || !delta || !theta || !phi)
         return set_error(FD_ERR_ARG, "tti_forward: epsilon, delta, theta and phi are required");
+    fd_tti_options op = {FD_TTI_CENTRED, FD_TTI_REC_P, FD_TTI_TWO_PASS};
+    if (opts) op = *opts;
+    if ((op.deriv != FD_TTI_CENTRED && op.deriv != FD_TTI_STAGGERED) ||
+        (op.receiver != FD_TTI_REC_P && op.receiver != FD_TTI_REC_MEAN) ||
+        (op.scheme != FD_TTI_TWO_PASS && op.scheme != FD_TTI_RECOMPUTE))
+        return set_error(FD_ERR_ARG, "tti_forward: options (%d, %d, %d) out of range", op.deriv,
+                         op.receiver, op.scheme);
+    const bool stag = op.deriv == FD_TTI_STAGGERED;
+    const bool two_pass = op.scheme == FD_TTI_TWO_PASS;
     const int R = so / 2;
     GridDerived gd = derive(grid, so);
     const WaveLayout &L = gd.L;
@@ -472,7 +508,7 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
     MediumStats *dstats;
     int *counter;
     ws.add(&wave, (size_t)4 * nshots * L.vol);  // p, r at two levels per shot
-    ws.add(&tmp, (size_t)6 * nshots * L.vol);   // pass-1 temporaries
+    ws.add(&tmp, two_pass ? (size_t)6 * nshots * L.vol : 0);  // pass-1 temporaries
     ws.add(&bcoef, (size_t)6 * L.vol);          // b, a, s, n_x, n_y, n_z
     ws.add(&dps, ndamp);
     ws.add(&src_tab, (size_t)nshots * nsrc);
@@ -516,7 +552,9 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
     {
         const double vmax = 1.0 / sqrt((double)hs.m_min);
         const double amax = 1.0 + 2.0 * (double)(hs.eps_max > 0.f ? hs.eps_max : 0.f);
-        const double sig = first_symbol_sq_max(R, gd.c);
+        double sa[kMaxRadius + 1];
+        staggered_weights(R, sa);
+        const double sig = stag ? staggered_symbol_sq_max(R, sa) : first_symbol_sq_max(R, gd.c);
         const double lam = sig * (1.0 / (grid->hx * grid->hx) + 1.0 / (grid->hy * grid->hy) +
                                   1.0 / (grid->hz * grid->hz));
         const double dt_max = 2.0 / sqrt(amax * vmax * vmax * lam);
@@ -534,7 +572,8 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
     }
 
     TtiPlan tplan;
-    FD_TRY(tti_plan(R, L, nshots, wave, tmp, bcoef, &tplan));
+    FD_TRY(tti_plan(R, L, nshots, wave, tmp, bcoef, &tplan, stag ? 1 : 0,
+                    two_pass ? kTtiTwoPass : kTtiRecompute));
     TtiArgs a;
     memset(&a, 0, sizeof(a));
     a.wave = wave;
@@ -549,10 +588,26 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
     a.L = L;
     a.nshots = nshots;
     a.err = &dstats->flags;
-    for (int k = 1; k <= R; ++k) {
-        a.cx[k] = (float)(gd.c[k] / grid->hx);
-        a.cy[k] = (float)(gd.c[k] / grid->hy);
-        a.cz[k] = (float)(gd.c[k] / grid->hz);
+    {
+        // tap tables (offset d at index d + R): centred sign(d) c_|d|;
+        // staggered inner D+ (a_d at +d, -a_d at 1-d), outer D- (a_d at d-1,
+        // -a_d at -d); all divided by the spacing of the axis
+        double sa[kMaxRadius + 1];
+        staggered_weights(R, sa);
+        const double hh[3] = {grid->hx, grid->hy, grid->hz};
+        for (int ax = 0; ax < 3; ++ax) {
+            for (int d = -R; d <= R; ++d) {
+                double w1 = 0.0, w2 = 0.0;
+                if (!stag) {
+                    w1 = w2 = d > 0 ? gd.c[d] : (d < 0 ? -gd.c[-d] : 0.0);
+                } else {
+                    w1 = d >= 1 ? sa[d] : (d > -R ? -sa[1 - d] : 0.0);
+                    w2 = d <= -1 ? -sa[-d] : (d < R ? sa[d + 1] : 0.0);
+                }
+                a.t1[ax][d + R] = (float)(w1 / hh[ax]);
+                a.t2[ax][d + R] = (float)(w2 / hh[ax]);
+            }
+        }
     }
     SparseArgs sp;
     memset(&sp, 0, sizeof(sp));
@@ -572,6 +627,7 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
     sp.nrec = nrec;
     sp.rec_tab = rec_tab;
     sp.rec_out = srec.dev;
+    sp.rec_mean = op.receiver == FD_TTI_REC_MEAN ? 1 : 0;
 
     const int nsteps = nt - 1;
     const bool timing = stats_enabled();
@@ -588,6 +644,7 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
         si.inj_level0 = 1 - par;
         si.inj_level1 = 3 - par;
         si.rec_level = par;
+        si.rec_level2 = 2 + par;
         si.step_base = via_counter ? counter : nullptr;
         FD_TRY(sparse_launch(si, i, nsrc > 0, nrec > 0, s));
         if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 3), s));
@@ -599,6 +656,7 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
     {
         SparseArgs si = sp;
         si.rec_level = last;
+        si.rec_level2 = 2 + last;
         si.step_base = nullptr;
         FD_TRY(sparse_launch(si, nt - 1, false, nrec > 0, s));
     }
@@ -624,8 +682,12 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
             t2 += evs.elapsed(i, 1, 2);
             ts += evs.elapsed(i, 2, 3);
         }
-        stats_add("tti_pass1", t1, nsteps, (double)dense * nshots);
-        stats_add("tti_pass2", t2, nsteps, (double)dense * nshots);
+        if (two_pass) {
+            stats_add("tti_pass1", t1, nsteps, (double)dense * nshots);
+            stats_add("tti_pass2", t2, nsteps, (double)dense * nshots);
+        } else {
+            stats_add("tti_recompute", t1, nsteps, (double)dense * nshots);
+        }
         stats_add("sparse", ts, nsteps, (double)(nrec + 16 * nsrc) * nshots);
     }
     ws.release();
@@ -1000,7 +1062,22 @@ fd_status tti_forward(const fd_grid *grid, int so, double dt, int nt, int nshots
     fdsweep::clear_error();
     return fdsweep::tti_forward_impl(grid, so, dt, nt, nshots, m, damp, epsilon, delta, theta,
                                      phi, nsrc, src_xyz, src_wav, nrec, rec_xyz, rec_out, p_init,
-                                     r_init, p_final, r_final, static_cast<cudaStream_t>(stream));
+                                     r_init, p_final, r_final, nullptr,
+                                     static_cast<cudaStream_t>(stream));
+}
+
+fd_status tti_forward_opts(const fd_grid *grid, int so, double dt, int nt, int nshots,
+                           const float *m, const float *damp, const float *epsilon,
+                           const float *delta, const float *theta, const float *phi, int nsrc,
+                           const float *src_xyz, const float *src_wav, int nrec,
+                           const float *rec_xyz, float *rec_out, const float *p_init,
+                           const float *r_init, float *p_final, float *r_final,
+                           const fd_tti_options *opts, void *stream) {
+    fdsweep::clear_error();
+    return fdsweep::tti_forward_impl(grid, so, dt, nt, nshots, m, damp, epsilon, delta, theta,
+                                     phi, nsrc, src_xyz, src_wav, nrec, rec_xyz, rec_out, p_init,
+                                     r_init, p_final, r_final, opts,
+                                     static_cast<cudaStream_t>(stream));
 }
 
 fd_status acoustic_adjoint(const fd_grid *grid, int so, double dt, int nt, int nshots,

@@ -104,6 +104,9 @@ struct SparseArgs {
     const SparsePoint *rec_tab;  // [nshots][nrec]
     float *rec_out;              // [nshots][nt][nrec]
     int rec_level;
+    // rec_mean != 0: record the mean of levels rec_level and rec_level2
+    // (the (p + r)/2 receiver reading of the TTI system)
+    int rec_mean, rec_level2;
     const int *step_base;        // device counter added to `step` (may be null)
 };
 
@@ -145,6 +148,13 @@ fd_status check_finite(const float *field, const WaveLayout &L, int nfields,
 
 // ---------------------------------------------------------------- TTI K2a/K2b
 
+// First-derivative stencils of the TTI operators as tap tables: entry d + R
+// (d = -R..R) of t[axis] weights the value at offset d along the axis,
+// already divided by h.  Centred: t[d] = sign(d) c_|d|.  Staggered: the inner
+// derivative (pass 1) is D+ (taps -R+1..R), the outer one (pass 2) D- (taps
+// -R..R-1).
+constexpr int kTaps = 2 * kMaxRadius + 1;
+
 struct TtiArgs {
     float *wave;           // 4 buffers per shot: p levels (0,1), r levels (2,3)
     float *tmp;            // 6 temporaries per shot [6][vol]
@@ -153,12 +163,17 @@ struct TtiArgs {
     WaveLayout L;
     int nshots;
     int cur;
-    float cx[kMaxRadius + 1], cy[kMaxRadius + 1], cz[kMaxRadius + 1];  // c_k / h_d
+    float t1[3][kTaps];    // inner first derivative (of p, r)
+    float t2[3][kTaps];    // outer first derivative (of the temporaries)
     unsigned int *err;
 };
 
+enum TtiScheme { kTtiTwoPass = 0, kTtiRecompute = 1 };
+
 struct TtiPlan {
     int radius = 0;
+    int stag = 0;    // 0: centred first derivatives, 1: staggered (D+ inner, D- outer)
+    int scheme = kTtiTwoPass;
     CUtensorMap map_wint, map_whalo;          // p/r buffers: interior, x+y halo boxes
     CUtensorMap map_tint, map_tx, map_ty;     // temporaries: interior, x-halo, y-halo
     CUtensorMap map_cint;                     // b, a, s, n_x, n_y, n_z: interior box
@@ -167,9 +182,12 @@ struct TtiPlan {
     int zchunk = 0, nzc = 1;
 };
 
-// coef: 6 consecutive fields b, a, s, n_x, n_y, n_z ([6][vol]).
+// coef: 6 consecutive fields b, a, s, n_x, n_y, n_z ([6][vol]).  scheme
+// kTtiTwoPass: K2a writes the six first-derivative temporaries and K2b
+// differentiates them again; kTtiRecompute: one kernel recomputes the inner
+// derivatives at every outer stencil point (no temporaries; tmp unused).
 fd_status tti_plan(int radius, const WaveLayout &L, int nshots, float *wave, float *tmp,
-                   const float *coef, TtiPlan *plan);
+                   const float *coef, TtiPlan *plan, int stag = 0, int scheme = kTtiTwoPass);
 fd_status tti_launch(const TtiPlan &plan, const TtiArgs &a, cudaStream_t stream,
                      cudaEvent_t *ev /* 3 events or null */);
 

@@ -37,8 +37,18 @@ __global__ void sparse_kernel(const SparseArgs a, int step, int do_inject, int64
         const SparsePoint p = a.rec_tab[gid];
         const float *u = a.wave + (int64_t)(s * a.fields_per_shot + a.rec_level) * a.L.vol;
         float acc = 0.f;
+        if (a.rec_mean) {  // interpolate (u + u2) / 2
+            const float *u2 = a.wave + (int64_t)(s * a.fields_per_shot + a.rec_level2) * a.L.vol;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc = fmaf(corner_weight(p, c), __ldg(u + corner_offset(p, c, a.L)), acc);
+            for (int c = 0; c < 8; ++c) {
+                const int64_t o = corner_offset(p, c, a.L);
+                acc = fmaf(corner_weight(p, c), 0.5f * (__ldg(u + o) + __ldg(u2 + o)), acc);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                acc = fmaf(corner_weight(p, c), __ldg(u + corner_offset(p, c, a.L)), acc);
+        }
         a.rec_out[((int64_t)s * a.nt + ro) * a.nrec + i] = acc;
         return;
     }

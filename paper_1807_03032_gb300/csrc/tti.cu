@@ -67,62 +67,69 @@ __device__ __forceinline__ float4 lds4(const float *p) {
     return *reinterpret_cast<const float4 *>(p);
 }
 
+// Stencil kinds: 0 centred (taps -R..R without the centre), +1 forward-
+// staggered D+ (taps -R+1..R), -1 backward-staggered D- (taps -R..R-1).
+template <int KIND>
+__host__ __device__ constexpr bool tap_used(int d, int R) {
+    return KIND == 0 ? d != 0 : (KIND > 0 ? d > -R : d < R);
+}
+
 // First derivative along x of 4 consecutive points from a row that starts RA
-// points left of them: sum_k c_k (q[+k] - q[-k]).
-template <int R, int RA>
-__device__ __forceinline__ float4 dx4(const float *row, const float *c) {
+// points left of them: sum_d t[d + R] q[d].
+template <int R, int RA, int KIND>
+__device__ __forceinline__ float4 dx4(const float *row, const float *t) {
     float xs[2 * RA + 4];
 #pragma unroll
-    for (int t = 0; t < (2 * RA + 4) / 4; ++t) {
-        const float4 f = lds4(row + 4 * t);
-        xs[4 * t] = f.x;
-        xs[4 * t + 1] = f.y;
-        xs[4 * t + 2] = f.z;
-        xs[4 * t + 3] = f.w;
+    for (int i = 0; i < (2 * RA + 4) / 4; ++i) {
+        const float4 f = lds4(row + 4 * i);
+        xs[4 * i] = f.x;
+        xs[4 * i + 1] = f.y;
+        xs[4 * i + 2] = f.z;
+        xs[4 * i + 3] = f.w;
     }
     float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int k = 1; k <= R; ++k) {
-        d.x = fmaf(c[k], xs[RA + 0 + k] - xs[RA + 0 - k], d.x);
-        d.y = fmaf(c[k], xs[RA + 1 + k] - xs[RA + 1 - k], d.y);
-        d.z = fmaf(c[k], xs[RA + 2 + k] - xs[RA + 2 - k], d.z);
-        d.w = fmaf(c[k], xs[RA + 3 + k] - xs[RA + 3 - k], d.w);
+    for (int k = -R; k <= R; ++k) {
+        if (!tap_used<KIND>(k, R)) continue;
+        const float w = t[k + R];
+        d.x = fmaf(w, xs[RA + 0 + k], d.x);
+        d.y = fmaf(w, xs[RA + 1 + k], d.y);
+        d.z = fmaf(w, xs[RA + 2 + k], d.z);
+        d.w = fmaf(w, xs[RA + 3 + k], d.w);
     }
     return d;
 }
 
 // First derivative along y: `centre` points at the thread's float4 in the
 // centre row, rows `pitch` floats apart.
-template <int R>
-__device__ __forceinline__ float4 dy4(const float *centre, int pitch, const float *c) {
+template <int R, int KIND>
+__device__ __forceinline__ float4 dy4(const float *centre, int pitch, const float *t) {
     float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int k = 1; k <= R; ++k) {
-        const float4 p = lds4(centre + k * pitch), m = lds4(centre - k * pitch);
-        d.x = fmaf(c[k], p.x - m.x, d.x);
-        d.y = fmaf(c[k], p.y - m.y, d.y);
-        d.z = fmaf(c[k], p.z - m.z, d.z);
-        d.w = fmaf(c[k], p.w - m.w, d.w);
+    for (int k = -R; k <= R; ++k) {
+        if (!tap_used<KIND>(k, R)) continue;
+        d = f4fma(t[k + R], lds4(centre + k * pitch), d);
     }
     return d;
 }
 
 // z first-derivative accumulator pipeline: acc[i] is output plane p-R+i when
-// plane p arrives with values c.  Returns nothing; acc[0] is then complete.
-template <int R>
-__device__ __forceinline__ void dz_feed(float4 (&acc)[2 * R], float4 c, const float *cz) {
+// plane p arrives with values c (plane p is at offset R - i from it); acc[0]
+// is then complete.
+template <int R, int KIND>
+__device__ __forceinline__ void dz_feed(float4 (&acc)[2 * R], float4 c, const float *t) {
 #pragma unroll
     for (int i = 0; i < 2 * R; ++i) {
-        if (i == R) continue;
-        const float w = i < R ? cz[R - i] : -cz[i - R];
-        acc[i] = f4fma(w, c, acc[i]);
+        if (!tap_used<KIND>(R - i, R)) continue;
+        acc[i] = f4fma(t[2 * R - i], c, acc[i]);
     }
 }
-template <int R>
-__device__ __forceinline__ void dz_shift(float4 (&acc)[2 * R], float4 c, const float *cz) {
+// rotate: the new last entry is output p+R, for which plane p is offset -R
+template <int R, int KIND>
+__device__ __forceinline__ void dz_shift(float4 (&acc)[2 * R], float4 c, const float *t) {
 #pragma unroll
     for (int i = 0; i < 2 * R - 1; ++i) acc[i] = acc[i + 1];
-    const float w = -cz[R];
+    const float w = tap_used<KIND>(-R, R) ? t[0] : 0.f;
     acc[2 * R - 1] = make_float4(w * c.x, w * c.y, w * c.z, w * c.w);
 }
 
@@ -153,7 +160,7 @@ __device__ __forceinline__ Ring ring_init(unsigned char *raw, size_t stage_float
 
 // ---------------------------------------------------------------- pass 1
 
-template <int R, int TX, int TY, int D>
+template <int R, int TX, int TY, int D, int KIND>
 __global__ void __launch_bounds__(2 * TX * TY)
     tti_pass1_kernel(const __grid_constant__ CUtensorMap map_wint,
                      const __grid_constant__ CUtensorMap map_whalo,
@@ -224,12 +231,13 @@ __global__ void __launch_bounds__(2 * TX * TY)
         const float *st = ring.smem + slot * C::STAGE1;
         const int q = ty * C::BX + 4 * tx;
         const float4 c = lds4(st + field * C::INT + q);
-        dz_feed<R>(acc, c, a.cz);
+        dz_feed<R, KIND>(acc, c, a.t1[2]);
         if (j >= 2 * R) {
             const int zs = za - 2 * R + j;
             const float *H = st + 2 * C::INT + field * C::HXY;
-            const float4 gxv = dx4<R, C::RA>(H + (R + ty) * C::PW + 4 * tx, a.cx);
-            const float4 gyv = dy4<R>(H + (R + ty) * C::PW + C::RA + 4 * tx, C::PW, a.cy);
+            const float4 gxv = dx4<R, C::RA, KIND>(H + (R + ty) * C::PW + 4 * tx, a.t1[0]);
+            const float4 gyv =
+                dy4<R, KIND>(H + (R + ty) * C::PW + C::RA + 4 * tx, C::PW, a.t1[1]);
             const float4 gzv = acc[0];
             const float *N = st + 2 * C::INT + 2 * C::HXY;
             const float4 nx = lds4(N + q), ny = lds4(N + C::INT + q), nz = lds4(N + 2 * C::INT + q);
@@ -257,7 +265,7 @@ __global__ void __launch_bounds__(2 * TX * TY)
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&ring.empty[slot]);
-        dz_shift<R>(acc, c, a.cz);
+        dz_shift<R, KIND>(acc, c, a.t1[2]);
     }
     __syncthreads();
     if (*ring.abort_flag && tid == 0)
@@ -268,7 +276,7 @@ __global__ void __launch_bounds__(2 * TX * TY)
 
 // ---------------------------------------------------------------- pass 2
 
-template <int R, int TX, int TY, int D>
+template <int R, int TX, int TY, int D, int KIND>
 __global__ void __launch_bounds__(2 * TX * TY)
     tti_pass2_kernel(const __grid_constant__ CUtensorMap map_tint,
                      const __grid_constant__ CUtensorMap map_tx,
@@ -359,15 +367,15 @@ __global__ void __launch_bounds__(2 * TX * TY)
         float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
         if (good) {
             c = lds4(st + field * C::INT + q);
-            dz_feed<R>(acc, c, a.cz);
+            dz_feed<R, KIND>(acc, c, a.t2[2]);
         }
         const bool outp = j >= 2 * R;
         float *xb = xchg + (j & 1) * 2 * C::INT;
         if (outp && good) {
             const float *hx = st + 2 * C::INT + field * C::HX;
             const float *hy = st + 2 * C::INT + 2 * C::HX + field * C::HY;
-            const float4 dxv = dx4<R, C::RA>(hx + ty * C::PW + 4 * tx, a.cx);
-            const float4 dyv = dy4<R>(hy + (R + ty) * C::BX + 4 * tx, C::BX, a.cy);
+            const float4 dxv = dx4<R, C::RA, KIND>(hx + ty * C::PW + 4 * tx, a.t2[0]);
+            const float4 dyv = dy4<R, KIND>(hy + (R + ty) * C::BX + 4 * tx, C::BX, a.t2[1]);
             const float4 v = f4add(f4add(dxv, dyv), acc[0]);  // A (field 0) or B (field 1)
             *reinterpret_cast<float4 *>(xb + field * C::INT + q) = v;
         }
@@ -403,7 +411,7 @@ __global__ void __launch_bounds__(2 * TX * TY)
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&ring.empty[slot]);
-        dz_shift<R>(acc, c, a.cz);
+        dz_shift<R, KIND>(acc, c, a.t2[2]);
     }
     __syncthreads();
     if (*ring.abort_flag && tid == 0)
@@ -412,56 +420,162 @@ __global__ void __launch_bounds__(2 * TX * TY)
                 mbar_wait_bounded(&ring.full[jj % C::NSL], (uint32_t)((jj / C::NSL) & 1), 200000000ull);
 }
 
+// ---------------------------------------------------------------- recompute
+
+// The "no temporaries" scheme of the ablation (the paper's `advanced` level:
+// common sub-expressions eliminated, but no shift-invariant temporaries): for
+// every outer stencil point of Hxy p = sum_i D_i f_i and Hz r = sum_i D_i e_i
+// the inner gradients of p and r, and from them f_i and e_i, are recomputed
+// from scratch.  Work per point grows as (stencil points)^2 instead of
+// linearly; the loads are served by L1/L2.  One thread per grid point; CHECK
+// adds the zero-ghost tests near the boundary (block-uniform choice).
+template <int R, int K1, int K2, bool CHECK>
+__device__ __forceinline__ void recompute_ops(const TtiArgs &a, const float *__restrict__ p,
+                                              const float *__restrict__ r, int i, int j, int k,
+                                              float &A, float &B) {
+    const WaveLayout &L = a.L;
+    const int64_t o0 = (int64_t)k * L.plane + (int64_t)j * L.nxp + i;
+    const int64_t stride[3] = {1, L.nxp, L.plane};
+    const int n3[3] = {L.nx, L.ny, L.nz};
+    const int c0[3] = {i, j, k};
+    A = 0.f;
+    B = 0.f;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+#pragma unroll 1
+        for (int d = -R; d <= R; ++d) {
+            if (!tap_used<K2>(d, R)) continue;
+            if (CHECK && (c0[ax] + d < 0 || c0[ax] + d >= n3[ax])) continue;  // zero ghost
+            const int64_t o2 = o0 + d * stride[ax];
+            float gp[3] = {0.f, 0.f, 0.f}, gr[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const int cb = c0[b] + (b == ax ? d : 0);
+#pragma unroll
+                for (int e = -R; e <= R; ++e) {
+                    if (!tap_used<K1>(e, R)) continue;
+                    if (CHECK && (cb + e < 0 || cb + e >= n3[b])) continue;
+                    const int64_t o3 = o2 + e * stride[b];
+                    const float w = a.t1[b][e + R];
+                    gp[b] = fmaf(w, __ldg(p + o3), gp[b]);
+                    gr[b] = fmaf(w, __ldg(r + o3), gr[b]);
+                }
+            }
+            const float nx = __ldg(a.nvec + o2), ny = __ldg(a.nvec + L.vol + o2),
+                        nz = __ldg(a.nvec + 2 * L.vol + o2);
+            const float hp = nx * gp[0] + ny * gp[1] + nz * gp[2];
+            const float hr = nx * gr[0] + ny * gr[1] + nz * gr[2];
+            const float na = ax == 0 ? nx : (ax == 1 ? ny : nz);
+            const float w2 = a.t2[ax][d + R];
+            A = fmaf(w2, gp[ax] - na * hp, A);  // f_ax = D_ax p - n_ax (n . grad p)
+            B = fmaf(w2, na * hr, B);           // e_ax = n_ax (n . grad r)
+        }
+    }
+}
+
+constexpr int kRecBX = 32, kRecBY = 8;
+
+template <int R, int K1, int K2>
+__global__ void __launch_bounds__(kRecBX *kRecBY) tti_recompute_kernel(const TtiArgs a) {
+    const WaveLayout &L = a.L;
+    const int i = blockIdx.x * kRecBX + threadIdx.x;
+    const int j = blockIdx.y * kRecBY + threadIdx.y;
+    const int shot = blockIdx.z / L.nz;
+    const int k = blockIdx.z - shot * L.nz;
+    // every tap of the block (outer + inner: 2R) inside the grid?
+    const int bx0 = blockIdx.x * kRecBX, by0 = blockIdx.y * kRecBY;
+    const bool interior = bx0 >= 2 * R && bx0 + kRecBX + 2 * R <= L.nx && by0 >= 2 * R &&
+                          by0 + kRecBY + 2 * R <= L.ny && k >= 2 * R && k + 2 * R < L.nz;
+    if (i >= L.nx || j >= L.ny) return;
+    const float *p = a.wave + (int64_t)(4 * shot + a.cur) * L.vol;
+    const float *r = a.wave + (int64_t)(4 * shot + 2 + a.cur) * L.vol;
+    float A, B;
+    if (interior)
+        recompute_ops<R, K1, K2, false>(a, p, r, i, j, k, A, B);
+    else
+        recompute_ops<R, K1, K2, true>(a, p, r, i, j, k, A, B);
+    const int64_t o = (int64_t)k * L.plane + (int64_t)j * L.nxp + i;
+    const float b = __ldg(a.bcoef + o), av = __ldg(a.acoef + o), sv = __ldg(a.scoef + o);
+    const float zeta = (a.dpx[i] + (a.dpy[j] + a.dpz[k])) * b;
+    const float *pm = a.wave + (int64_t)(4 * shot + 1 - a.cur) * L.vol;
+    const float *rm = a.wave + (int64_t)(4 * shot + 3 - a.cur) * L.vol;
+    const float pc = __ldg(p + o), pp = pm[o], rc = __ldg(r + o), rp = rm[o];
+    const float rhs_p = av * A + sv * B, rhs_r = sv * A + B;
+    // q+ overwrites q- (each point reads q- only at itself)
+    a.wave[(int64_t)(4 * shot + 1 - a.cur) * L.vol + o] = pc + (1.f - zeta) * (pc - pp) + b * rhs_p;
+    a.wave[(int64_t)(4 * shot + 3 - a.cur) * L.vol + o] = rc + (1.f - zeta) * (rc - rp) + b * rhs_r;
+}
+
 // ---------------------------------------------------------------- host side
 
 constexpr int kTX = 16, kTY = 8;  // 64 x 8 tile, two groups of 128 threads
 
 // Prefetch depth per pass: pass 2 stages carry eleven tiles, so for the wide
 // stencils one slot less keeps two CTAs per SM.
-template <int R>
+template <int R, int STAG>
 struct TtiKernels {
     static constexpr int D1 = 2;
     static constexpr int D2 = R >= 6 ? 1 : 2;
+    static constexpr int K1 = STAG ? 1 : 0;   // inner derivative: D+ or centred
+    static constexpr int K2 = STAG ? -1 : 0;  // outer derivative: D- or centred
     using C1 = TtiCfg<R, kTX, kTY, D1>;
     using C2 = TtiCfg<R, kTX, kTY, D2>;
-    static const void *p1() { return (const void *)&tti_pass1_kernel<R, kTX, kTY, D1>; }
-    static const void *p2() { return (const void *)&tti_pass2_kernel<R, kTX, kTY, D2>; }
+    static const void *p1() { return (const void *)&tti_pass1_kernel<R, kTX, kTY, D1, K1>; }
+    static const void *p2() { return (const void *)&tti_pass2_kernel<R, kTX, kTY, D2, K2>; }
+    static const void *rc() { return (const void *)&tti_recompute_kernel<R, K1, K2>; }
 };
 
 struct TtiInfo {
-    const void *p1, *p2;
+    const void *p1, *p2, *rc;
     size_t smem1, smem2;
     int bx, by, pw, ph, threads;
 };
 
-template <int R>
+template <int R, int STAG>
 TtiInfo info_r() {
-    using K = TtiKernels<R>;
+    using K = TtiKernels<R, STAG>;
     using C1 = typename K::C1;
     using C2 = typename K::C2;
     static_assert(C1::BX == C2::BX && C1::BY == C2::BY && C1::THREADS == C2::THREADS, "tiles");
-    return TtiInfo{K::p1(), K::p2(), C1::SMEM1, C2::SMEM2, C1::BX, C1::BY, C1::PW, C1::PH,
+    return TtiInfo{K::p1(), K::p2(), K::rc(), C1::SMEM1, C2::SMEM2, C1::BX, C1::BY, C1::PW, C1::PH,
                    C1::THREADS};
 }
 
-bool tti_info(int radius, TtiInfo *out) {
+template <int STAG>
+bool tti_info_s(int radius, TtiInfo *out) {
     switch (radius) {
-        case 1: *out = info_r<1>(); return true;
-        case 2: *out = info_r<2>(); return true;
-        case 4: *out = info_r<4>(); return true;
-        case 6: *out = info_r<6>(); return true;
-        case 8: *out = info_r<8>(); return true;
+        case 1: *out = info_r<1, STAG>(); return true;
+        case 2: *out = info_r<2, STAG>(); return true;
+        case 4: *out = info_r<4, STAG>(); return true;
+        case 6: *out = info_r<6, STAG>(); return true;
+        case 8: *out = info_r<8, STAG>(); return true;
         default: return false;
     }
+}
+
+bool tti_info(int radius, int stag, TtiInfo *out) {
+    return stag ? tti_info_s<1>(radius, out) : tti_info_s<0>(radius, out);
 }
 
 }  // namespace
 
 fd_status tti_plan(int radius, const WaveLayout &L, int nshots, float *wave, float *tmp,
-                   const float *coef, TtiPlan *plan) {
+                   const float *coef, TtiPlan *plan, int stag, int scheme) {
     TtiInfo in;
-    if (!tti_info(radius, &in)) return set_error(FD_ERR_SO, "no TTI kernel for radius %d", radius);
+    if (!tti_info(radius, stag, &in))
+        return set_error(FD_ERR_SO, "no TTI kernel for radius %d", radius);
     plan->radius = radius;
+    plan->stag = stag ? 1 : 0;
+    plan->scheme = scheme;
+    if (scheme == kTtiRecompute) {
+        if ((int64_t)nshots * L.nz > 65535)
+            return set_error(FD_ERR_ARG, "grid too large for the TTI recompute launch");
+        plan->grid = dim3((L.nx + kRecBX - 1) / kRecBX, (L.ny + kRecBY - 1) / kRecBY,
+                          nshots * L.nz);
+        plan->block = dim3(kRecBX, kRecBY, 1);
+        return FD_OK;
+    }
+    if (scheme != kTtiTwoPass) return set_error(FD_ERR_ARG, "unknown TTI scheme %d", scheme);
     int dev = 0, nsm = 0, per_sm = 0;
     FD_CUDA_TRY(cudaGetDevice(&dev));
     FD_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -506,9 +620,19 @@ fd_status tti_plan(int radius, const WaveLayout &L, int nshots, float *wave, flo
 fd_status tti_launch(const TtiPlan &plan, const TtiArgs &a, cudaStream_t stream,
                      cudaEvent_t *ev) {
     TtiInfo in;
-    if (!tti_info(plan.radius, &in)) return set_error(FD_ERR_SO, "bad TTI plan");
+    if (!tti_info(plan.radius, plan.stag, &in)) return set_error(FD_ERR_SO, "bad TTI plan");
     int zchunk = plan.zchunk, nzc = plan.nzc;
     if (ev) FD_CUDA_TRY(cudaEventRecord(ev[0], stream));
+    if (plan.scheme == kTtiRecompute) {
+        void *pr[] = {(void *)&a};
+        FD_CUDA_TRY(cudaLaunchKernel(in.rc, plan.grid, plan.block, pr, 0, stream));
+        note_launch(stream);
+        if (ev) {
+            FD_CUDA_TRY(cudaEventRecord(ev[1], stream));
+            FD_CUDA_TRY(cudaEventRecord(ev[2], stream));
+        }
+        return FD_OK;
+    }
     void *p1[] = {(void *)&plan.map_wint, (void *)&plan.map_whalo, (void *)&plan.map_cint,
                   (void *)&a, (void *)&zchunk, (void *)&nzc};
     FD_CUDA_TRY(cudaLaunchKernel(in.p1, plan.grid, plan.block, p1, plan.smem1, stream));
