@@ -44,6 +44,9 @@ import workloads  # noqa: E402
 
 SO_LIST = (4, 8, 12, 16)
 BYTES_PER_POINT_ACOUSTIC = 16.0  # read u^n, u^{n-1}, b; write u^{n+1}
+BYTES_PER_POINT_STEP2 = 20.0     # two steps: read u^n, u^{n-1}, b; write u^{n+1}, u^{n+2}
+ACOUSTIC_KERNELS = (("acoustic_step", BYTES_PER_POINT_ACOUSTIC, 1),
+                    ("acoustic_step2", BYTES_PER_POINT_STEP2, 2))
 BYTES_PER_POINT_TTI = 44.0       # p, r: read 2 levels + write 1 (24 B); m, eps, delta, theta, phi (20 B)
 METRIC = "GPts/s (acoustic 512^3, so 4/8/12/16)"
 
@@ -72,14 +75,33 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("acoustic.cu", "kernels.cuh", "common.cuh"):
+    for f in ("acoustic.cu", "acoustic2.cu", "f32x2.cuh", "kernels.cuh", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1807_03032_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
+def acoustic_kernel_stats(_native):
+    """{family: (total ms, launches, points per launch)} of the acoustic
+    stencil kernels from the library's statistics."""
+    return {f: _native.stats_get(f) for f, _, _ in ACOUSTIC_KERNELS}
+
+
+def roofline_of(family, st, peak, peak_kind, traffic=None):
+    bpp = dict((f, b) for f, b, _ in ACOUSTIC_KERNELS)[family]
+    ms, n, pts = st
+    launch_ms = ms / max(n, 1)
+    achieved = bpp * pts / (launch_ms * 1e-3) / 1e9 if n else 0.0
+    return {"bound": "hbm", "kernel": family, "achieved": round(achieved, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+            if peak_kind == "measured" else "fallback 6.8 TB/s",
+            "bytes_per_point": bpp, "launch_ms": round(launch_ms, 4), "launches": int(n)}
+
+
 def ncu_traffic():
-    """Per-launch DRAM bytes of acoustic_step from the committed ncu summary,
-    or None if the kernel source changed since it was captured."""
+    """Per-launch DRAM bytes of the acoustic kernels from the committed ncu
+    summary ({family: {so: bytes}}), or None if the kernel sources changed
+    since it was captured."""
     p = os.path.join(ROOT, "profiles", "acoustic_step_traffic.json")
     if not os.path.exists(p):
         return None
@@ -187,6 +209,9 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     _native.load()
+    for so in args.so:
+        if args.time_tiling == -1 or _native.num_time_tiling_configs(so) > 0:
+            _native.set_time_tiling(so, args.time_tiling)
 
     n = args.n
     t0 = time.time()
@@ -242,7 +267,7 @@ def run_ours(args):
     barrier()
     clocks = sampler.stop()
     launches = _native.launch_count() - launches0
-    k1_ms, k1_n, k1_pts = _native.stats_get("acoustic_step")
+    kst = acoustic_kernel_stats(_native)
     sp_ms, sp_n, _ = _native.stats_get("sparse")
     _native.stats_enable(False)
     elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), ws, dev)
@@ -255,33 +280,47 @@ def run_ours(args):
     for so in args.so:
         per_so[str(so)] = {"gpts": round(points_per_forward * args.steps / (per_so_ms[so] * 1e-3) / 1e9, 2)}
     peak, peak_kind = measured_peaks()
-    k1_launch_ms = k1_ms / max(k1_n, 1)
-    achieved = BYTES_PER_POINT_ACOUSTIC * k1_pts / (k1_launch_ms * 1e-3) / 1e9
-    traffic = None
-    tr = ncu_traffic()
-    if tr:
-        vals = [tr["bytes_per_launch"].get(str(so)) for so in args.so]
-        if all(v is not None for v in vals):
-            traffic = float(np.mean(vals)) * (k1_pts / tr.get("points_per_launch", k1_pts))
-    roofline = {"bound": "hbm", "kernel": "acoustic_step", "achieved": round(achieved, 1),
-                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": traffic, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
-                if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "bytes_per_point": BYTES_PER_POINT_ACOUSTIC,
-                "launch_ms": round(k1_launch_ms, 4), "launches": k1_n,
-                "sparse_launch_ms": round(sp_ms / max(sp_n, 1), 4)}
-
-    # per-so kernel rooflines (separate short timed passes, one forward each)
+    # per space order: kernels, steps and algorithmic bytes (separate short
+    # timed passes, one forward each)
+    so_kernel = {}
     for so in args.so:
         _native.stats_reset()
         _native.stats_enable(True)
         fd.acoustic_forward(g, so, w.dt, w.nt, m, sxyz, swav, rxyz, damp=damp, rec_out=rec_out,
                             return_final=False)
-        ms_, n_, pts_ = _native.stats_get("acoustic_step")
+        st = acoustic_kernel_stats(_native)
         _native.stats_enable(False)
-        a_ = BYTES_PER_POINT_ACOUSTIC * pts_ / (ms_ / n_ * 1e-3) / 1e9
-        per_so[str(so)].update({"kernel_gbs": round(a_, 1), "kernel_frac": round(a_ / peak, 4),
-                                "kernel_gpts": round(pts_ / (ms_ / n_ * 1e-3) / 1e9, 2)})
+        kms = sum(v[0] for v in st.values())
+        steps = sum(st[f][1] * k for f, _, k in ACOUSTIC_KERNELS)
+        pts_ = max(v[2] for v in st.values())
+        alg = sum(b * st[f][1] * st[f][2] for f, b, _ in ACOUSTIC_KERNELS)
+        main = max(st, key=lambda f: st[f][0])
+        so_kernel[so] = main
+        per_so[str(so)].update({
+            "kernel": main, "kernel_gbs": round(alg / (kms * 1e-3) / 1e9, 1),
+            "kernel_frac": round(alg / (kms * 1e-3) / 1e9 / peak, 4),
+            "kernel_gpts": round(pts_ * steps / (kms * 1e-3) / 1e9, 2),
+            "bytes_per_point_step": round(alg / (pts_ * steps), 2)})
+
+    # roofline of the dominant kernel of the timed region (by device time),
+    # and of every acoustic stencil kernel that ran
+    tr = ncu_traffic()
+    rooflines = {}
+    for fam, _, _ in ACOUSTIC_KERNELS:
+        if kst[fam][1] == 0:
+            continue
+        traffic = None
+        if tr and fam in tr:
+            sos = [so for so in args.so if so_kernel.get(so) == fam]
+            vals = [tr[fam].get(str(so)) for so in sos]
+            if sos and all(v is not None for v in vals):
+                traffic = float(np.mean(vals)) * (kst[fam][2] / tr.get("points_per_launch",
+                                                                        kst[fam][2]))
+        rooflines[fam] = roofline_of(fam, kst[fam], peak, peak_kind, traffic)
+    dominant = max(rooflines, key=lambda f: kst[f][0])
+    roofline = dict(rooflines[dominant])
+    roofline["sparse_launch_ms"] = round(sp_ms / max(sp_n, 1), 4)
+    roofline["others"] = {f: r for f, r in rooflines.items() if f != dominant}
 
     # ---------------------------------------------------------------- end to end (host buffers)
     e2e = None
@@ -653,6 +692,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tti", action="store_true")
     ap.add_argument("--no-tti-ablation", action="store_true")
+    ap.add_argument("--time-tiling", type=int, default=-1,
+                    help="fd_set_time_tiling mode for every space order (-1 automatic, "
+                         "0 off, 1 + k two-step kernel configuration k)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fwi", action="store_true")
     ap.add_argument("--no-serving", action="store_true")

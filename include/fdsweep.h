@@ -307,8 +307,10 @@ const char *fd_version(void);
  * entry points launch their time loop without CUDA graphs and bracket every
  * stencil-kernel launch with CUDA events on the call's stream; the elapsed
  * times are accumulated per kernel family when the call completes.
- * Families: "acoustic_step", "tti_pass1", "tti_pass2", "tti_recompute" (the
- * one-kernel TTI scheme of tti_forward_opts), "sparse".
+ * Families: "acoustic_step", "acoustic_step2" (two time steps per launch, see
+ * fd_set_time_tiling; points_per_launch counts the points of one step),
+ * "tti_pass1", "tti_pass2", "tti_recompute" (the one-kernel TTI scheme of
+ * tti_forward_opts), "sparse".
  * fd_stats_get returns FD_ERR_ARG for an unknown family.
  */
 fd_status fd_stats_enable(int on);
@@ -319,6 +321,25 @@ fd_status fd_stats_get(const char *family, double *total_ms, int64_t *launches,
 /* Number of kernel launches this library has enqueued since it was loaded
  * (a replayed CUDA graph counts each of its kernel nodes). */
 int64_t fd_launch_count(void);
+
+/*
+ * Time tiling of acoustic_forward (loop blocking across the time dimension,
+ * named in the paper's section "Further work"): two leapfrog
+ * steps per kernel launch, the intermediate level kept in shared memory and
+ * its halo recomputed by neighbouring tiles; results are bit-identical to
+ * single steps.  Applies to space orders with a two-step kernel
+ * (fd_num_time_tiling_configs(so) > 0), at most 16 sources per shot and
+ * nt >= 3; it uses four wavefield levels per shot instead of two.
+ *   mode -1  automatic (the default; off for every space order, since two
+ *            single steps measured faster on GB300: the single-step kernel
+ *            is near the HBM bound, the two-step one issue-bound),
+ *         0  off,
+ *     1 + k  on, with configuration k of the two-step kernel.
+ * Process-wide setting, not synchronised with calls in flight.  Returns
+ * FD_ERR_SO / FD_ERR_ARG for an unknown space order or mode.
+ */
+fd_status fd_set_time_tiling(int so, int mode);
+int fd_num_time_tiling_configs(int so);
 
 /*
  * Tile configuration override for the acoustic stencil kernel (for tuning

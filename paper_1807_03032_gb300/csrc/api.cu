@@ -96,6 +96,29 @@ double staggered_symbol_sq_max(int r, const double *a) {
 bool valid_so(int so) { return so == 2 || so == 4 || so == 8 || so == 12 || so == 16; }
 
 int g_acoustic_config[kMaxRadius + 1] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
+// Time tiling per radius: -1 automatic, 0 off, 1 + k forced with configuration k.
+int g_time_tiling[kMaxRadius + 1] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
+
+// Radii for which the two-step kernel is the automatic choice: none.  On
+// GB300 the single-step kernel runs at 95 % of the HBM copy bandwidth for
+// so = 4, and the two-step kernel, which recomputes the extended tile's halo
+// and stages three more tiles per plane, is bound by instruction issue and
+// shared memory instead: 0.83 ms per two steps at 512^3 (so = 4) against
+// 2 x 0.335 ms for two single steps; 2.5x slower at so = 8.
+bool time_tiling_auto(int R) {
+    (void)R;
+    return false;
+}
+
+// Whether acoustic_forward runs its time loop two steps per launch, and with
+// which configuration of the time-tiled kernel.
+bool use_time_tiling(int R, int nsrc, int nsteps, int *config) {
+    const int mode = g_time_tiling[R];
+    *config = mode > 0 ? mode - 1 : 0;
+    if (mode == 0 || nsteps < 2 || nsrc > kStep2MaxSources || acoustic2_num_configs(R) == 0)
+        return false;
+    return mode > 0 || time_tiling_auto(R);
+}
 
 fd_status validate_common(const fd_grid *g, int so, double dt, int nt, int nshots, const float *m,
                           int nsrc, const float *src_xyz, const float *src_wav, int nrec,
@@ -308,6 +331,10 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     const WaveLayout &L = gd.L;
     const size_t dense = (size_t)L.nx * L.ny * L.nz;
     const int ndamp = L.nx + L.ny + L.nz;
+    // two steps per launch needs four distinct levels per shot
+    int t2_config = 0;
+    const bool tiled = use_time_tiling(R, nsrc, nt - 1, &t2_config);
+    const int lps = tiled ? 4 : 2;
 
     CallStream cs;
     FD_TRY(cs.begin(caller));
@@ -318,7 +345,7 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     SparsePoint *src_tab, *rec_tab;
     MediumStats *dstats;
     int *counter;
-    ws.add(&wave, (size_t)2 * nshots * L.vol);  // u at two levels per shot
+    ws.add(&wave, (size_t)lps * nshots * L.vol);  // u levels per shot
     ws.add(&bcoef, L.vol);                      // b = dt^2 / (m + damp dt/2)
     ws.add(&dps, ndamp);                        // damping / dt
     ws.add(&src_tab, (size_t)nshots * nsrc);
@@ -367,14 +394,15 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     }
 
     // ---- initial state
-    FD_CUDA_TRY(cudaMemsetAsync(wave, 0, (size_t)2 * nshots * L.vol * 4, s));
+    FD_CUDA_TRY(cudaMemsetAsync(wave, 0, (size_t)lps * nshots * L.vol * 4, s));
     if (u_init)
-        for (int sh = 0; sh < nshots; ++sh) FD_TRY(copy_fields_in(wave, L, u_init, sh, 2, 2, 0, s));
+        for (int sh = 0; sh < nshots; ++sh)
+            FD_TRY(copy_fields_in(wave, L, u_init, sh, 2, lps, 0, s));
 
     // ---- K1 plan and arguments
     AcousticPlan plan;
     FD_STAGE(s, "acoustic: initial state");
-    FD_TRY(acoustic_plan(R, g_acoustic_config[R], L, nshots, 2, wave, bcoef, &plan));
+    FD_TRY(acoustic_plan(R, g_acoustic_config[R], L, nshots, lps, wave, bcoef, &plan));
     FD_STAGE(s, plan.name);
     AcousticStepArgs a;
     memset(&a, 0, sizeof(a));
@@ -397,7 +425,7 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     SparseArgs sp;
     memset(&sp, 0, sizeof(sp));
     sp.wave = wave;
-    sp.fields_per_shot = 2;
+    sp.fields_per_shot = lps;
     sp.L = L;
     sp.bcoef = bcoef;
     sp.nshots = nshots;
@@ -417,53 +445,141 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     // ---- time loop
     const int nsteps = nt - 1;
     const bool timing = stats_enabled();
+    const bool graphs = !timing && trace_level() < 2;
+    int last = nsteps & 1, prev_of_last = 1 - last;  // levels of u^{nt-1}, u^{nt-2}
+    // per-launch events (stats mode): one row per step, or per pair plus one
+    // row for a final single step; read after the call's closing sync
+    const int nunits = tiled ? nsteps / 2 : nsteps;
     StepEvents evs;
-    if (timing) FD_TRY(evs.create(nsteps, 3));
-    auto step = [&](int i, int par, bool via_counter) -> fd_status {
-        AcousticStepArgs ai = a;
-        set_two_levels(ai, par);
-        if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 0), s));
-        FD_TRY(acoustic_launch(plan, ai, s));
-        if (!via_counter && trace_level() >= 2) FD_STAGE(s, "acoustic_step kernel");
-        if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 1), s));
-        SparseArgs si = sp;
-        si.inj_level0 = 1 - par;
-        si.rec_level = par;
-        si.step_base = via_counter ? counter : nullptr;
-        FD_TRY(sparse_launch(si, i, nsrc > 0, nrec > 0, s));
-        if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 2), s));
-        return FD_OK;
-    };
-    FD_TRY(run_time_loop(nsteps, s, counter, !timing && trace_level() < 2, step));
+    if (timing) FD_TRY(evs.create(nunits + 1, 3));
+    bool odd_tail = false;
+    if (!tiled) {
+        auto step = [&](int i, int par, bool via_counter) -> fd_status {
+            AcousticStepArgs ai = a;
+            set_two_levels(ai, par);
+            if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 0), s));
+            FD_TRY(acoustic_launch(plan, ai, s));
+            if (!via_counter && trace_level() >= 2) FD_STAGE(s, "acoustic_step kernel");
+            if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 1), s));
+            SparseArgs si = sp;
+            si.inj_level0 = 1 - par;
+            si.rec_level = par;
+            si.step_base = via_counter ? counter : nullptr;
+            FD_TRY(sparse_launch(si, i, nsrc > 0, nrec > 0, s));
+            if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 2), s));
+            return FD_OK;
+        };
+        FD_TRY(run_time_loop(nsteps, s, counter, graphs, step));
+    } else {
+        // Two steps per launch over four levels per shot: pair i (parity par)
+        // reads u^n, u^{n-1} from levels (0, 1) or (3, 2) and writes u^{n+1},
+        // u^{n+2} to (2, 3) or (1, 0), so every pair starts where the one
+        // before the previous did.  The sparse kernel records rec[n] and
+        // rec[n+1] and injects src[n+1] into u^{n+2}; src[n] is injected into
+        // u^{n+1} by the two-step kernel itself.
+        Acoustic2Plan plan2;
+        FD_TRY(acoustic2_plan(R, t2_config, L, nshots, lps, wave, bcoef, &plan2));
+        FD_STAGE(s, plan2.name);
+        AcousticStep2Args a2;
+        memset(&a2, 0, sizeof(a2));
+        a2.s = a;
+        a2.s.lps = lps;
+        a2.src_tab = nsrc > 0 ? src_tab : nullptr;
+        a2.src_wav = swav.dev;
+        a2.nsrc = nsrc;
+        a2.nt = nt;
+        const int npairs = nunits;
+        auto pair = [&](int i, int par, bool via_counter) -> fd_status {
+            AcousticStep2Args ai = a2;
+            ai.s.lev_cur = par ? 3 : 0;
+            ai.s.lev_prev = par ? 2 : 1;
+            ai.s.lev_out = par ? 1 : 2;
+            ai.lev_out2 = par ? 0 : 3;
+            ai.step = i;
+            ai.step_base = via_counter ? counter : nullptr;
+            if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 0), s));
+            FD_TRY(acoustic2_launch(plan2, ai, s));
+            if (!via_counter && trace_level() >= 2) FD_STAGE(s, "acoustic_step2 kernel");
+            if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 1), s));
+            SparseArgs si = sp;
+            si.inj_level0 = ai.lev_out2;
+            si.inj_t0 = 1;
+            si.inj_dt = 2;
+            si.rec_level = ai.s.lev_cur;
+            si.rec_t0 = 0;
+            si.rec_dt = 2;
+            si.step_base = ai.step_base;
+            FD_TRY(sparse_launch(si, i, nsrc > 0, nrec > 0, s));
+            SparseArgs sj = sp;
+            sj.rec_level = ai.s.lev_out;
+            sj.rec_t0 = 1;
+            sj.rec_dt = 2;
+            sj.step_base = ai.step_base;
+            FD_TRY(sparse_launch(sj, i, false, nrec > 0, s));
+            if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 2), s));
+            return FD_OK;
+        };
+        FD_TRY(run_time_loop(npairs, s, counter, graphs, pair));
+        last = (npairs & 1) ? 3 : 0;
+        prev_of_last = (npairs & 1) ? 2 : 1;
+        if (nsteps & 1) {  // one single step to finish, in place
+            AcousticStepArgs ai = a;
+            ai.lps = lps;
+            ai.lev_cur = last;
+            ai.lev_prev = prev_of_last;
+            ai.lev_out = prev_of_last;
+            if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(nunits, 0), s));
+            FD_TRY(acoustic_launch(plan, ai, s));
+            if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(nunits, 1), s));
+            SparseArgs si = sp;
+            si.inj_level0 = prev_of_last;
+            si.rec_level = last;
+            FD_TRY(sparse_launch(si, nsteps - 1, nsrc > 0, nrec > 0, s));
+            if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(nunits, 2), s));
+            odd_tail = true;
+            const int t = last;
+            last = prev_of_last;
+            prev_of_last = t;
+        }
+    }
     FD_STAGE(s, "acoustic: time loop");
-    const int last = nsteps & 1;  // level holding u^{nt-1}
     {
         SparseArgs si = sp;
         si.rec_level = last;
         si.step_base = nullptr;
         FD_TRY(sparse_launch(si, nt - 1, false, nrec > 0, s));
     }
-    FD_TRY(check_finite(wave, L, 2 * nshots, &dstats->flags, s));
+    FD_TRY(check_finite(wave, L, lps * nshots, &dstats->flags, s));
     FD_STAGE(s, "acoustic: final interpolation and check");
 
     // ---- outputs
     if (u_final) {
         for (int sh = 0; sh < nshots; ++sh) {
             float *dst = u_final + (size_t)sh * 2 * dense;
-            FD_TRY(copy_field_out(dst, wave + (int64_t)(2 * sh + last) * L.vol, L, s));
-            FD_TRY(copy_field_out(dst + dense, wave + (int64_t)(2 * sh + 1 - last) * L.vol, L, s));
+            FD_TRY(copy_field_out(dst, wave + (int64_t)(lps * sh + last) * L.vol, L, s));
+            FD_TRY(copy_field_out(dst + dense, wave + (int64_t)(lps * sh + prev_of_last) * L.vol,
+                                  L, s));
         }
     }
     FD_TRY(srec.copy_back(s));
     FD_TRY(read_stats(dstats, &hs, s));
     if (timing && nsteps > 0) {
-        double k1 = 0.0, spm = 0.0;
-        for (int i = 0; i < nsteps; ++i) {
-            k1 += evs.elapsed(i, 0, 1);
-            spm += evs.elapsed(i, 1, 2);
+        double kms = 0.0, sms = 0.0;
+        for (int i = 0; i < nunits; ++i) {
+            kms += evs.elapsed(i, 0, 1);
+            sms += evs.elapsed(i, 1, 2);
         }
-        stats_add("acoustic_step", k1, nsteps, (double)dense * nshots);
-        stats_add("sparse", spm, nsteps, (double)(nrec + 8 * nsrc) * nshots);
+        const double pts = (double)dense * nshots;
+        if (tiled) {
+            if (nunits) stats_add("acoustic_step2", kms, nunits, pts);
+            if (odd_tail) {
+                stats_add("acoustic_step", evs.elapsed(nunits, 0, 1), 1, pts);
+                sms += evs.elapsed(nunits, 1, 2);
+            }
+        } else {
+            stats_add("acoustic_step", kms, nunits, pts);
+        }
+        stats_add("sparse", sms, nsteps, (double)(nrec + 8 * nsrc) * nshots);
     }
     ws.release();
     FD_TRY(cs.finish());
@@ -1112,6 +1228,21 @@ fd_status fd_stats_reset(void) { return fdsweep::stats_reset(); }
 fd_status fd_stats_get(const char *family, double *total_ms, int64_t *launches,
                        double *points_per_launch) {
     return fdsweep::stats_get(family, total_ms, launches, points_per_launch);
+}
+
+fd_status fd_set_time_tiling(int so, int mode) {
+    fdsweep::clear_error();
+    if (!fdsweep::valid_so(so)) return fdsweep::set_error(FD_ERR_SO, "space order %d", so);
+    const int R = so / 2;
+    if (mode < -1 || mode > fdsweep::acoustic2_num_configs(R))
+        return fdsweep::set_error(FD_ERR_ARG, "time tiling mode %d out of range for so = %d",
+                                  mode, so);
+    fdsweep::g_time_tiling[R] = mode;
+    return FD_OK;
+}
+
+int fd_num_time_tiling_configs(int so) {
+    return fdsweep::valid_so(so) ? fdsweep::acoustic2_num_configs(so / 2) : 0;
 }
 
 fd_status fd_set_acoustic_config(int so, int config) {

@@ -82,6 +82,39 @@ fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots,
 fd_status acoustic_launch(const AcousticPlan &plan, const AcousticStepArgs &args,
                           cudaStream_t stream);
 
+// ---------------------------------------------------------------- time-tiled K1
+
+// Two leapfrog steps per launch (acoustic2.cu): u^n (lev_cur), u^{n-1}
+// (lev_prev) -> u^{n+1} (lev_out) and u^{n+2} (lev_out2), all distinct levels;
+// src[n] (n = 2 (step + *step_base)) is injected into u^{n+1} in the kernel.
+constexpr int kStep2MaxSources = 16;
+
+struct AcousticStep2Args {
+    AcousticStepArgs s;          // slot_map must be null
+    int lev_out2;
+    const SparsePoint *src_tab;  // [nshots][nsrc] or null
+    const float *src_wav;        // [nshots][nt][nsrc]
+    int nsrc, nt;
+    const int *step_base;        // device pair counter (may be null)
+    int step;                    // pair index added to *step_base
+};
+
+struct Acoustic2Plan {
+    int radius = 0;
+    int config = 0;
+    CUtensorMap map_halo, map_ext, map_int, map_bext, map_bint;
+    dim3 grid, block;
+    size_t smem = 0;
+    int zchunk = 0, nzc = 1;
+    const char *name = "";
+};
+
+int acoustic2_num_configs(int radius);  // 0: no time-tiled kernel for this radius
+fd_status acoustic2_plan(int radius, int config, const WaveLayout &L, int nshots, int lps,
+                         float *wave, const float *bcoef, Acoustic2Plan *plan);
+fd_status acoustic2_launch(const Acoustic2Plan &plan, const AcousticStep2Args &args,
+                           cudaStream_t stream);
+
 // ---------------------------------------------------------------- sparse K3/K4
 
 struct SparseArgs {
