@@ -1,6 +1,7 @@
 // setup.cu -- K0: per-call coefficient precompute and validation.
 //
-//  * b = dt^2 / (m + damp dt / 2) per point (FP64 arithmetic, rounded once),
+//  * b = dt^2 / (m + damp dt / 2) per point (FP64 arithmetic, the reciprocal
+//    by Newton-Raphson, rounded once to FP32),
 //    the factor that multiplies the Laplacian in the leapfrog update and the
 //    injected source (Listing finject's dt^2 q / m, generalised to the damped
 //    update); damping profiles scaled by 1/dt.
@@ -54,26 +55,44 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
+// 1/x in FP64 by Newton-Raphson on the reciprocal (y <- y + y (1 - x y),
+// which squares the relative error), seeded with the FP32 reciprocal: two
+// steps take the 24-bit seed past FP64 precision.  GB300's FP64 rate is low,
+// and this costs a third of a full-precision division.  Falls back to the
+// division when the seed is not usable (x outside the FP32 normal range).
+__device__ __forceinline__ double recip_newton(double x) {
+    const float xf = (float)x;
+    if (!(fabsf(xf) >= 1.17549435e-38f && fabsf(xf) <= 1.0e38f)) return 1.0 / x;
+    double y = (double)__frcp_rn(xf);
+    y = fma(y, fma(-x, y, 1.0), y);
+    y = fma(y, fma(-x, y, 1.0), y);
+    return y;
+}
+
+// One grid row (j, k) per block iteration: the row index is split once per
+// row, not per point.
 __global__ void acoustic_coeff_kernel(const float *__restrict__ m, const float *__restrict__ damp,
                                       double dt, WaveLayout L, float *__restrict__ bcoef,
                                       StatsKeys *stats) {
-    const int64_t n = (int64_t)L.nx * L.ny * L.nz;
+    const int64_t rows = (int64_t)L.ny * L.nz;
+    const double dt2 = dt * dt;
     float lmin = __int_as_float(0x7f800000), lmax = 0.f;
     unsigned int bad = 0u;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(p % L.nx);
-        const int64_t r = p / L.nx;
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
         const int j = (int)(r % L.ny);
         const int k = (int)(r / L.ny);
-        const float mv = m[p];
-        double d = 0.0;
-        if (damp) d = (double)damp[i] + (double)damp[L.nx + j] + (double)damp[L.nx + L.ny + k];
-        if (!(mv > 0.f) || !isfinite(mv) || !(d >= 0.0) || !isfinite(d)) bad = DEV_ERR_MEDIUM;
-        lmin = fminf(lmin, mv);
-        lmax = fmaxf(lmax, mv);
-        const double b = dt * dt / ((double)mv + 0.5 * d * dt);
-        bcoef[(int64_t)k * L.plane + (int64_t)j * L.nxp + i] = (float)b;
+        const float dyf = damp ? damp[L.nx + j] : 0.f, dzf = damp ? damp[L.nx + L.ny + k] : 0.f;
+        const float *mrow = m + r * L.nx;
+        float *brow = bcoef + (int64_t)k * L.plane + (int64_t)j * L.nxp;
+        for (int i = threadIdx.x; i < L.nx; i += blockDim.x) {
+            const float mv = mrow[i];
+            double d = 0.0;
+            if (damp) d = (double)damp[i] + (double)dyf + (double)dzf;
+            if (!(mv > 0.f) || !isfinite(mv) || !(d >= 0.0) || !isfinite(d)) bad = DEV_ERR_MEDIUM;
+            lmin = fminf(lmin, mv);
+            lmax = fmaxf(lmax, mv);
+            brow[i] = (float)(dt2 * recip_newton((double)mv + 0.5 * d * dt));
+        }
     }
     lmin = warp_min(lmin);
     lmax = warp_max(lmax);
@@ -188,8 +207,8 @@ fd_status setup_acoustic_coeffs(const float *m, const float *damp, double dt,
                                 const WaveLayout &L, float *bcoef, float *dps,
                                 MediumStats *dev_stats, cudaStream_t stream) {
     StatsKeys *keys = reinterpret_cast<StatsKeys *>(dev_stats);
-    const int64_t n = (int64_t)L.nx * L.ny * L.nz;
-    acoustic_coeff_kernel<<<grid_for(n, 256), 256, 0, stream>>>(m, damp, dt, L, bcoef, keys);
+    acoustic_coeff_kernel<<<grid_for((int64_t)L.ny * L.nz * 256, 256), 256, 0, stream>>>(
+        m, damp, dt, L, bcoef, keys);
     FD_CUDA_TRY(cudaGetLastError());
     note_launch(stream);
     const int nd = L.nx + L.ny + L.nz;
