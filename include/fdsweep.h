@@ -210,8 +210,11 @@ fd_status acoustic_adjoint(const fd_grid *grid, int so, double dt, int nt, int n
  *   src_wav   [nshots][nt][nsrc]  source wavelets of the forward model.
  *   rec_resid [nshots][nt][nrec]  residual traces.
  *   grad_m    [nz][ny][nx]        output.
- *   Device memory: 4 + K + 2 + 2 ceil((nt-1)/K) wavefield volumes, K the
- *   checkpoint interval.  Other arguments as for acoustic_forward.
+ *   Device memory: 4 + K + 2 + 2 ceil((nt-1)/K) wavefield volumes per shot
+ *   of a batch, K the checkpoint interval; shots are stepped together in
+ *   batches of as many as fit in 80 % of the free device memory (at least
+ *   one; the environment variable FDSWEEP_GRAD_BATCH=n caps the batch).
+ *   Other arguments as for acoustic_forward.
  */
 fd_status acoustic_gradient(const fd_grid *grid, int so, double dt, int nt, int nshots,
                             const float *m, const float *damp, int nsrc, const float *src_xyz,

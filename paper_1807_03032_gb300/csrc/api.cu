@@ -10,6 +10,7 @@
 // the sparse kernel reads its time index from a device counter that the
 // graph's last node advances.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <vector>
@@ -981,7 +982,8 @@ static fd_status acoustic_adjoint_impl(const fd_grid *grid, int so, double dt, i
 // ====================================================================== gradient
 
 /*
- * FWI gradient: grad m = d<dd, d(m)>/dm, summed over shots.  Forward with a
+ * FWI gradient: grad m = d<dd, d(m)>/dm, summed over shots (in batches of
+ * shots stepped together, as many as the device memory holds).  Forward with a
  * checkpoint (u^t, u^{t-1}) every K steps; then, segment by segment from the
  * last, the forward states of the segment are recomputed from its checkpoint
  * and the adjoint w (see acoustic_adjoint) is stepped back through it while
@@ -1012,16 +1014,34 @@ static fd_status acoustic_gradient_impl(const fd_grid *grid, int so, double dt, 
     CallStream cs;
     FD_TRY(cs.begin(caller));
     cudaStream_t s = cs.get();
+    // Shots are processed in batches of B (one stencil launch per step for the
+    // whole batch); B is bounded by the device memory the per-shot buffers
+    // (forward and adjoint pairs, the segment, the checkpoints) need.
+    const int64_t vol = L.vol;
+    const int64_t per_shot = (int64_t)(4 + (K + 2) + 2 * (nseg > 0 ? nseg : 1)) * vol * 4;
+    int B = 1;
+    {
+        size_t free_b = 0, total_b = 0;
+        FD_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+        const int64_t fixed = (int64_t)(4 + 2) * vol * 4 +
+                              (int64_t)nshots * (int64_t)nt * (nrec + nsrc) * 4;
+        const int64_t budget = (int64_t)(0.8 * (double)free_b) - fixed;
+        const int64_t fit = per_shot > 0 ? budget / per_shot : 1;
+        B = (int)(fit < 1 ? 1 : (fit > nshots ? nshots : fit));
+        // FDSWEEP_GRAD_BATCH=n caps the batch (to exercise several batches)
+        const char *cap = getenv("FDSWEEP_GRAD_BATCH");
+        if (cap && atoi(cap) > 0 && atoi(cap) < B) B = atoi(cap);
+    }
     Workspace ws;
     float *fwd, *adj, *seg, *ckpt, *grad, *bcoef, *dps;
     SparsePoint *src_tab, *rec_tab;
     MediumStats *dstats;
-    ws.add(&fwd, (size_t)2 * L.vol);
-    ws.add(&adj, (size_t)2 * L.vol);
-    ws.add(&seg, (size_t)(K + 2) * L.vol);
-    ws.add(&ckpt, (size_t)2 * (nseg > 0 ? nseg : 1) * L.vol);
-    ws.add(&grad, L.vol);
-    ws.add(&bcoef, L.vol);
+    ws.add(&fwd, (size_t)2 * B * vol);
+    ws.add(&adj, (size_t)2 * B * vol);
+    ws.add(&seg, (size_t)(K + 2) * B * vol);
+    ws.add(&ckpt, (size_t)2 * (nseg > 0 ? nseg : 1) * B * vol);
+    ws.add(&grad, vol);
+    ws.add(&bcoef, vol);
     ws.add(&dps, ndamp);
     ws.add(&src_tab, (size_t)nshots * nsrc);
     ws.add(&rec_tab, (size_t)nshots * nrec);
@@ -1040,44 +1060,46 @@ static fd_status acoustic_gradient_impl(const fd_grid *grid, int so, double dt, 
     FD_TRY(acoustic_common_setup(grid, so, dt, gd, nshots, sm.dev, sdamp.dev, nsrc, ssxyz.dev,
                                  nrec, srxyz.dev, bcoef, dps, src_tab, rec_tab, dstats,
                                  "acoustic_gradient", s));
-    FD_CUDA_TRY(cudaMemsetAsync(grad, 0, (size_t)L.vol * 4, s));
-    AcousticPlan pf, pa, ps;
-    FD_TRY(acoustic_plan(R, g_acoustic_config[R], L, 1, 2, fwd, bcoef, &pf));
-    FD_TRY(acoustic_plan(R, g_acoustic_config[R], L, 1, 2, adj, bcoef, &pa));
-    FD_TRY(acoustic_plan(R, g_acoustic_config[R], L, 1, K + 2, seg, bcoef, &ps));
-    AcousticStepArgs af, aa, as;
-    fill_step_args(af, grid, gd, fwd, bcoef, dps, 1, &dstats->flags);
-    fill_step_args(aa, grid, gd, adj, bcoef, dps, 1, &dstats->flags);
-    fill_step_args(as, grid, gd, seg, bcoef, dps, 1, &dstats->flags);
-    const size_t vb = (size_t)L.vol * 4;
-    for (int sh = 0; sh < nshots && nsteps > 0; ++sh) {
-        // sources of this shot injected into a one-shot buffer set
+    FD_CUDA_TRY(cudaMemsetAsync(grad, 0, (size_t)vol * 4, s));
+    const size_t vb = (size_t)vol * 4;
+    for (int s0 = 0; s0 < nshots && nsteps > 0; s0 += B) {
+        const int nb = nshots - s0 < B ? nshots - s0 : B;
+        AcousticPlan pf, pa, ps;
+        FD_TRY(acoustic_plan(R, g_acoustic_config[R], L, nb, 2, fwd, bcoef, &pf));
+        FD_TRY(acoustic_plan(R, g_acoustic_config[R], L, nb, 2, adj, bcoef, &pa));
+        FD_TRY(acoustic_plan(R, g_acoustic_config[R], L, nb, K + 2, seg, bcoef, &ps));
+        AcousticStepArgs af, aa, as;
+        fill_step_args(af, grid, gd, fwd, bcoef, dps, nb, &dstats->flags);
+        fill_step_args(aa, grid, gd, adj, bcoef, dps, nb, &dstats->flags);
+        fill_step_args(as, grid, gd, seg, bcoef, dps, nb, &dstats->flags);
+        // sources of the batch's shots, and residuals injected at their receivers
         SparseArgs src;
         memset(&src, 0, sizeof(src));
         src.L = L;
         src.bcoef = bcoef;
-        src.nshots = 1;
+        src.nshots = nb;
         src.nt = nt;
         src.nsrc = nsrc;
-        src.src_tab = src_tab + (size_t)sh * nsrc;
-        src.src_wav = swav.dev ? swav.dev + (size_t)sh * nt * nsrc : nullptr;
+        src.src_tab = src_tab + (size_t)s0 * nsrc;
+        src.src_wav = swav.dev ? swav.dev + (size_t)s0 * nt * nsrc : nullptr;
         src.inj_level1 = -1;
         src.inj_dt = 1;
         src.rec_dt = 1;
-        SparseArgs res = src;  // residuals injected at the receivers
+        SparseArgs res = src;
         res.nsrc = nrec;
-        res.src_tab = rec_tab + (size_t)sh * nrec;
-        res.src_wav = sres.dev + (size_t)sh * nt * nrec;
-        // 1. forward with checkpoints
-        FD_CUDA_TRY(cudaMemsetAsync(fwd, 0, 2 * vb, s));
+        res.src_tab = rec_tab + (size_t)s0 * nrec;
+        res.src_wav = sres.dev + (size_t)s0 * nt * nrec;
+        // 1. forward with checkpoints: ckpt[c] holds (u^{cK-1}, u^{cK}) of every
+        //    shot of the batch ([nseg][nb][2][vol])
+        FD_CUDA_TRY(cudaMemsetAsync(fwd, 0, 2 * nb * vb, s));
         for (int t = 0; t < nsteps; ++t) {
             const int cur = t & 1;
             if (t % K == 0) {
-                const int c = t / K;
-                FD_CUDA_TRY(cudaMemcpyAsync(ckpt + (size_t)(2 * c) * L.vol, fwd + (size_t)(1 - cur) * L.vol,
-                                            vb, cudaMemcpyDeviceToDevice, s));
-                FD_CUDA_TRY(cudaMemcpyAsync(ckpt + (size_t)(2 * c + 1) * L.vol, fwd + (size_t)cur * L.vol,
-                                            vb, cudaMemcpyDeviceToDevice, s));
+                float *dst = ckpt + (size_t)(t / K) * 2 * nb * vol;
+                FD_CUDA_TRY(cudaMemcpy2DAsync(dst, 2 * vb, fwd + (size_t)(1 - cur) * vol, 2 * vb,
+                                              vb, nb, cudaMemcpyDeviceToDevice, s));
+                FD_CUDA_TRY(cudaMemcpy2DAsync(dst + vol, 2 * vb, fwd + (size_t)cur * vol, 2 * vb,
+                                              vb, nb, cudaMemcpyDeviceToDevice, s));
             }
             AcousticStepArgs ai = af;
             set_two_levels(ai, cur);
@@ -1089,7 +1111,7 @@ static fd_status acoustic_gradient_impl(const fd_grid *grid, int so, double dt, 
             FD_TRY(sparse_launch(si, t, nsrc > 0, false, s));
         }
         // 2. adjoint state: w^{nt-1} = B R^T dd^{nt-1} in level acur, w^{nt} = 0
-        FD_CUDA_TRY(cudaMemsetAsync(adj, 0, 2 * vb, s));
+        FD_CUDA_TRY(cudaMemsetAsync(adj, 0, 2 * nb * vb, s));
         int acur = 0;
         {
             SparseArgs si = res;
@@ -1104,9 +1126,10 @@ static fd_status acoustic_gradient_impl(const fd_grid *grid, int so, double dt, 
         for (int c = nseg - 1; c >= 0; --c) {
             const int t0 = c * K;
             const int kmax = (c + 1) * K < nsteps ? (c + 1) * K : nsteps;
-            // seg level l holds u^{t0 - 1 + l}
-            FD_CUDA_TRY(cudaMemcpyAsync(seg, ckpt + (size_t)(2 * c) * L.vol, 2 * vb,
-                                        cudaMemcpyDeviceToDevice, s));
+            // seg level l of every shot holds u^{t0 - 1 + l}
+            FD_CUDA_TRY(cudaMemcpy2DAsync(seg, (size_t)(K + 2) * vb,
+                                          ckpt + (size_t)c * 2 * nb * vol, 2 * vb, 2 * vb, nb,
+                                          cudaMemcpyDeviceToDevice, s));
             for (int t = t0 + 1; t <= kmax; ++t) {
                 AcousticStepArgs ai = as;
                 ai.lps = K + 2;
@@ -1121,9 +1144,9 @@ static fd_status acoustic_gradient_impl(const fd_grid *grid, int so, double dt, 
                 FD_TRY(sparse_launch(si, t - 1, nsrc > 0, false, s));
             }
             for (int k = kmax; k >= t0 + 1; --k) {
-                const float *uk = seg + (size_t)(k - t0 + 1) * L.vol;
-                FD_TRY(grad_accumulate(grad, adj + (size_t)acur * L.vol, uk, uk - L.vol,
-                                       uk - 2 * L.vol, L.vol, s));
+                FD_TRY(grad_accumulate_batch(grad, adj + (size_t)acur * vol, 2 * vol,
+                                             seg + (size_t)(k - t0 + 1) * vol,
+                                             (int64_t)(K + 2) * vol, nb, vol, s));
                 if (k >= 2) {
                     // w^{k-1} = M1 w^k - M2 w^{k+1} + B R^T dd^{k-1}
                     AcousticStepArgs ai = aa;
@@ -1140,7 +1163,7 @@ static fd_status acoustic_gradient_impl(const fd_grid *grid, int so, double dt, 
                 }
             }
         }
-        FD_STAGE(s, "gradient: shot done");
+        FD_STAGE(s, "gradient: shot batch done");
     }
     FD_TRY(scale_field(grad, (float)(-1.0 / (dt * dt)), L.vol, s));
     FD_TRY(check_finite(grad, L, 1, &dstats->flags, s));

@@ -148,10 +148,13 @@ struct SparseArgs {
 fd_status sparse_launch(const SparseArgs &a, int step, bool do_inject, bool do_interp,
                         cudaStream_t stream);
 fd_status bump_counter(int *counter, int by, cudaStream_t stream);
-// grad += w * (u0 - 2 u1 + u2) over `n` floats (the FWI imaging condition of
-// one time step; scaled by -1/dt^2 once at the end).
-fd_status grad_accumulate(float *grad, const float *w, const float *u0, const float *u1,
-                          const float *u2, int64_t n, cudaStream_t stream);
+// grad += sum_b w_b (u_b - 2 u_b' + u_b'') over `n` floats, the FWI imaging
+// condition of one time step for nb shots (scaled by -1/dt^2 once at the end):
+// w_b = w + b w_stride, u_b = u + b u_stride is the level of u^k and u_b',
+// u_b'' (u^{k-1}, u^{k-2}) are the n and 2n floats below it; shots are
+// accumulated in order.
+fd_status grad_accumulate_batch(float *grad, const float *w, int64_t w_stride, const float *u,
+                                int64_t u_stride, int nb, int64_t n, cudaStream_t stream);
 fd_status scale_field(float *f, float s, int64_t n, cudaStream_t stream);
 
 // ---------------------------------------------------------------- setup K0

@@ -72,20 +72,23 @@ __global__ void sparse_kernel(const SparseArgs a, int step, int do_inject, int64
 
 __global__ void bump_kernel(int *counter, int by) { *counter += by; }
 
-__global__ void grad_kernel(float *__restrict__ g, const float *__restrict__ w,
-                            const float *__restrict__ u0, const float *__restrict__ u1,
-                            const float *__restrict__ u2, int64_t n4) {
+// g += sum_b w_b (u_b - 2 u_b' + u_b''), shots b in order; u_b' and u_b'' are
+// the two levels below u_b (one field apart).  Strides and n in float4 units.
+__global__ void grad_batch_kernel(float *__restrict__ g, const float *__restrict__ w,
+                                  int64_t w_stride, const float *__restrict__ u,
+                                  int64_t u_stride, int64_t level, int nb, int64_t n4) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const float4 a = reinterpret_cast<const float4 *>(w)[i];
-        const float4 p = reinterpret_cast<const float4 *>(u0)[i];
-        const float4 q = reinterpret_cast<const float4 *>(u1)[i];
-        const float4 r = reinterpret_cast<const float4 *>(u2)[i];
         float4 o = reinterpret_cast<float4 *>(g)[i];
-        o.x = fmaf(a.x, p.x - 2.f * q.x + r.x, o.x);
-        o.y = fmaf(a.y, p.y - 2.f * q.y + r.y, o.y);
-        o.z = fmaf(a.z, p.z - 2.f * q.z + r.z, o.z);
-        o.w = fmaf(a.w, p.w - 2.f * q.w + r.w, o.w);
+        for (int b = 0; b < nb; ++b) {
+            const float4 a = reinterpret_cast<const float4 *>(w)[b * w_stride + i];
+            const float4 *ub = reinterpret_cast<const float4 *>(u) + b * u_stride + i;
+            const float4 p = ub[0], q = ub[-level], r = ub[-2 * level];
+            o.x = fmaf(a.x, p.x - 2.f * q.x + r.x, o.x);
+            o.y = fmaf(a.y, p.y - 2.f * q.y + r.y, o.y);
+            o.z = fmaf(a.z, p.z - 2.f * q.z + r.z, o.z);
+            o.w = fmaf(a.w, p.w - 2.f * q.w + r.w, o.w);
+        }
         reinterpret_cast<float4 *>(g)[i] = o;
     }
 }
@@ -129,10 +132,12 @@ fd_status bump_counter(int *counter, int by, cudaStream_t stream) {
     return FD_OK;
 }
 
-fd_status grad_accumulate(float *grad, const float *w, const float *u0, const float *u1,
-                          const float *u2, int64_t n, cudaStream_t stream) {
-    if (n % 4) return set_error(FD_ERR_ARG, "grad_accumulate: length not a multiple of 4");
-    grad_kernel<<<stream_grid(n / 4, 256), 256, 0, stream>>>(grad, w, u0, u1, u2, n / 4);
+fd_status grad_accumulate_batch(float *grad, const float *w, int64_t w_stride, const float *u,
+                                int64_t u_stride, int nb, int64_t n, cudaStream_t stream) {
+    if (n % 4 || w_stride % 4 || u_stride % 4)
+        return set_error(FD_ERR_ARG, "grad_accumulate_batch: sizes not multiples of 4");
+    grad_batch_kernel<<<stream_grid(n / 4, 256), 256, 0, stream>>>(grad, w, w_stride / 4, u,
+                                                                   u_stride / 4, n / 4, nb, n / 4);
     FD_CUDA_TRY(cudaGetLastError());
     note_launch(stream);
     return FD_OK;

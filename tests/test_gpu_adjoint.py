@@ -130,3 +130,25 @@ def test_autograd_gradients_and_central_difference():
     fd_est = (J_of(m0t + dm) - J_of(m0t - dm)) / 2.0
     an = float((gm.double() * dm.double()).sum())
     assert abs(fd_est - an) <= 2e-2 * abs(an), (fd_est, an)
+
+
+def test_gradient_shot_batches_sum_the_shots(monkeypatch):
+    """Five shots processed in batches of 2, 2, 1 and in one batch give the
+    same gradient (up to the order of FP32 accumulation), and it matches the
+    oracle."""
+    torch = require_cuda()
+    import paper_1807_03032_gb300 as fd
+    shape, h, so, dt, nt, m, damp, src, wav, rec = problem(so=8, nt=24, nshots=5, seed=5)
+    dd = np.random.default_rng(9).standard_normal((5, nt, rec.shape[1])).astype(np.float32)
+    g = fd.Grid(shape, h)
+    mt, dampt, srct, wavt, rect, ddt = to_dev(torch, m, damp, src, wav, rec, dd)
+    whole = fd.acoustic_gradient(g, so, dt, nt, mt, srct, wavt, rect, ddt, damp=dampt,
+                                 checkpoint_every=7).cpu().numpy()
+    monkeypatch.setenv("FDSWEEP_GRAD_BATCH", "2")
+    parts = fd.acoustic_gradient(g, so, dt, nt, mt, srct, wavt, rect, ddt, damp=dampt,
+                                 checkpoint_every=7).cpu().numpy()
+    torch.cuda.synchronize()
+    assert rel_l2(parts, whole) <= 1e-6
+    ref = oracle.acoustic_gradient(oracle.make_grid(shape, h), so, dt, nt, m, src, wav, rec, dd,
+                                   damp=damp)
+    assert rel_l2(whole, ref) <= TOL
