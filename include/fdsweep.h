@@ -345,6 +345,16 @@ fd_status fd_set_time_tiling(int so, int mode);
 int fd_num_time_tiling_configs(int so);
 
 /*
+ * Launch configuration override of the two TTI passes (prefetch depths and
+ * loop unroll; for tuning sweeps): index into the compiled table for the
+ * given space order (0 .. fd_num_tti_configs(so) - 1), or -1 for the
+ * built-in choice.  Applies to centred derivatives; the staggered reading
+ * always uses the built-in choice.  Process-wide; FD_ERR_ARG if out of range.
+ */
+fd_status fd_set_tti_config(int so, int config);
+int fd_num_tti_configs(int so);
+
+/*
  * Tile configuration override for the acoustic stencil kernel (for tuning
  * sweeps): index into the compiled configuration table for the given space
  * order, or -1 for the built-in choice.  Returns FD_ERR_ARG if out of range.

@@ -28,7 +28,7 @@ EXPORTED = ("acoustic_forward", "tti_forward", "tti_forward_opts", "fd_last_erro
             "acoustic_adjoint", "acoustic_gradient", "fd_engine_footprint", "fd_engine_create",
             "fd_engine_add_shot", "fd_engine_step", "fd_engine_shot_status", "fd_engine_release",
             "fd_engine_stream", "fd_engine_sync", "fd_engine_destroy", "fd_set_time_tiling",
-            "fd_num_time_tiling_configs")
+            "fd_num_time_tiling_configs", "fd_set_tti_config", "fd_num_tti_configs")
 
 
 class FdGrid(ctypes.Structure):
@@ -100,6 +100,10 @@ def load(path: str = LIB_PATH):
         lib.fd_stats_get.argtypes = [ctypes.c_char_p, ctypes.POINTER(D),
                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D)]
         lib.fd_stats_get.restype = I
+        lib.fd_set_tti_config.argtypes = [I, I]
+        lib.fd_set_tti_config.restype = I
+        lib.fd_num_tti_configs.argtypes = [I]
+        lib.fd_num_tti_configs.restype = I
         lib.fd_set_time_tiling.argtypes = [I, I]
         lib.fd_set_time_tiling.restype = I
         lib.fd_num_time_tiling_configs.argtypes = [I]
@@ -123,7 +127,7 @@ def load(path: str = LIB_PATH):
         for name in ("fd_engine_footprint", "fd_engine_create", "fd_engine_add_shot",
                      "fd_engine_step", "fd_engine_shot_status", "fd_engine_release",
                      "fd_engine_stream", "fd_engine_sync", "fd_engine_destroy", "fd_set_time_tiling",
-            "fd_num_time_tiling_configs"):
+            "fd_num_time_tiling_configs", "fd_set_tti_config", "fd_num_tti_configs"):
             getattr(lib, name).restype = I
         lib.fd_launch_count.argtypes = []
         lib.fd_launch_count.restype = ctypes.c_int64
@@ -167,6 +171,14 @@ def stats_get(family: str):
 def launch_count() -> int:
     """Kernel launches enqueued by the library since it was loaded."""
     return int(load().fd_launch_count())
+
+
+def set_tti_config(so: int, config: int):
+    check(load().fd_set_tti_config(int(so), int(config)))
+
+
+def num_tti_configs(so: int) -> int:
+    return int(load().fd_num_tti_configs(int(so)))
 
 
 def set_time_tiling(so: int, mode: int):

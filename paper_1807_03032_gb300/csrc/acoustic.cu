@@ -324,35 +324,38 @@ ConfigEntry make_entry(const char *name) {
 
 const ConfigEntry *config_table(int radius, int *count) {
     // Index 0 is the default; the others are kept for tuning sweeps
-    // (fd_set_acoustic_config).  Defaults measured on GB300 at 512^3: the
-    // plane-loop unroll U = 4 gains 2 % at R = 2 and 10 % at R = 6; at R = 4
-    // and R = 8 it gains nothing, and U = 2R costs occupancy (registers).
+    // (fd_set_acoustic_config).  Defaults measured on GB300 at 512^3 (template
+    // arguments R, TX, TY, VY, D, U): the plane-loop unroll U = 4 helps at every
+    // radius; a deeper prefetch suits R = 4 (D = 4, +10 %), a shallower one
+    // R = 8 (D = 1: more CTAs per SM).
     static const ConfigEntry r1[] = {FD_AC_ENTRY(1, 16, 16, 1, 4, 1)};
     static const ConfigEntry r2[] = {
-        FD_AC_ENTRY(2, 16, 16, 1, 4, 4), FD_AC_ENTRY(2, 16, 16, 1, 6, 1),
+        FD_AC_ENTRY(2, 16, 16, 1, 4, 4), FD_AC_ENTRY(2, 16, 16, 1, 4, 1),
         FD_AC_ENTRY(2, 16, 8, 1, 6, 1),  FD_AC_ENTRY(2, 16, 8, 2, 4, 1),
-        FD_AC_ENTRY(2, 16, 16, 1, 4, 2), FD_AC_ENTRY(2, 16, 16, 1, 4, 1)};
+        FD_AC_ENTRY(2, 16, 16, 1, 4, 2), FD_AC_ENTRY(2, 16, 16, 1, 3, 4),
+        FD_AC_ENTRY(2, 16, 16, 1, 5, 4), FD_AC_ENTRY(2, 16, 8, 1, 6, 4)};
     static const ConfigEntry r4[] = {
-        FD_AC_ENTRY(4, 16, 8, 1, 3, 1),  FD_AC_ENTRY(4, 16, 8, 1, 5, 1),
+        FD_AC_ENTRY(4, 16, 8, 1, 4, 4),  FD_AC_ENTRY(4, 16, 8, 1, 3, 1),
         FD_AC_ENTRY(4, 16, 16, 1, 4, 1), FD_AC_ENTRY(4, 16, 8, 2, 3, 1),
-        FD_AC_ENTRY(4, 16, 8, 1, 3, 2),  FD_AC_ENTRY(4, 16, 8, 1, 3, 4),
-        FD_AC_ENTRY(4, 16, 8, 1, 3, 8)};
+        FD_AC_ENTRY(4, 16, 8, 1, 3, 4),  FD_AC_ENTRY(4, 16, 16, 1, 3, 4),
+        FD_AC_ENTRY(4, 16, 8, 1, 5, 4),  FD_AC_ENTRY(4, 16, 8, 1, 6, 4),
+        FD_AC_ENTRY(4, 16, 8, 1, 4, 2),  FD_AC_ENTRY(4, 16, 8, 1, 4, 8)};
     static const ConfigEntry r6[] = {
-        FD_AC_ENTRY(6, 16, 8, 1, 2, 4),  FD_AC_ENTRY(6, 16, 8, 1, 4, 1),
+        FD_AC_ENTRY(6, 16, 8, 1, 3, 4),  FD_AC_ENTRY(6, 16, 8, 1, 2, 4),
         FD_AC_ENTRY(6, 16, 16, 1, 3, 1), FD_AC_ENTRY(6, 8, 16, 1, 3, 1),
-        FD_AC_ENTRY(6, 16, 8, 1, 2, 2),  FD_AC_ENTRY(6, 16, 8, 1, 2, 1),
-        FD_AC_ENTRY(6, 16, 8, 1, 2, 12)};
+        FD_AC_ENTRY(6, 16, 8, 1, 2, 1),  FD_AC_ENTRY(6, 16, 8, 1, 3, 2),
+        FD_AC_ENTRY(6, 16, 8, 1, 4, 4),  FD_AC_ENTRY(6, 16, 8, 1, 1, 4)};
     static const ConfigEntry r8[] = {
-        FD_AC_ENTRY(8, 16, 8, 1, 2, 1),  FD_AC_ENTRY(8, 16, 8, 1, 4, 1),
+        FD_AC_ENTRY(8, 16, 8, 1, 1, 4),  FD_AC_ENTRY(8, 16, 8, 1, 2, 1),
         FD_AC_ENTRY(8, 16, 16, 1, 3, 1), FD_AC_ENTRY(8, 8, 16, 1, 3, 1),
-        FD_AC_ENTRY(8, 16, 8, 1, 2, 2),  FD_AC_ENTRY(8, 16, 8, 1, 2, 4),
-        FD_AC_ENTRY(8, 16, 8, 1, 2, 16)};
+        FD_AC_ENTRY(8, 16, 8, 1, 2, 4),  FD_AC_ENTRY(8, 16, 8, 1, 1, 2),
+        FD_AC_ENTRY(8, 8, 16, 1, 1, 4),  FD_AC_ENTRY(8, 16, 8, 1, 1, 8)};
     switch (radius) {
         case 1: *count = 1; return r1;
-        case 2: *count = 6; return r2;
-        case 4: *count = 7; return r4;
-        case 6: *count = 7; return r6;
-        case 8: *count = 7; return r8;
+        case 2: *count = 8; return r2;
+        case 4: *count = 10; return r4;
+        case 6: *count = 8; return r6;
+        case 8: *count = 8; return r8;
         default: *count = 0; return nullptr;
     }
 }

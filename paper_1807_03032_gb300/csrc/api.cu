@@ -97,6 +97,8 @@ double staggered_symbol_sq_max(int r, const double *a) {
 bool valid_so(int so) { return so == 2 || so == 4 || so == 8 || so == 12 || so == 16; }
 
 int g_acoustic_config[kMaxRadius + 1] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
+// TTI pass configuration per radius (-1: default).
+int g_tti_config[kMaxRadius + 1] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
 // Time tiling per radius: -1 automatic, 0 off, 1 + k forced with configuration k.
 int g_time_tiling[kMaxRadius + 1] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
 
@@ -455,19 +457,31 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     if (timing) FD_TRY(evs.create(nunits + 1, 3));
     bool odd_tail = false;
     if (!tiled) {
+        // The receivers of step n read only u^n, which the stencil kernel of
+        // step n reads too and the kernel of step n+1 overwrites: they run on
+        // a side stream concurrently with the stencil, and only the source
+        // injection into u^{n+1} stays between two stencil launches.
+        SideLane side;
+        const bool overlap = nrec > 0;
+        if (overlap) FD_TRY(side.begin());
         auto step = [&](int i, int par, bool via_counter) -> fd_status {
             AcousticStepArgs ai = a;
             set_two_levels(ai, par);
-            if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 0), s));
-            FD_TRY(acoustic_launch(plan, ai, s));
-            if (!via_counter && trace_level() >= 2) FD_STAGE(s, "acoustic_step kernel");
-            if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 1), s));
             SparseArgs si = sp;
             si.inj_level0 = 1 - par;
             si.rec_level = par;
             si.step_base = via_counter ? counter : nullptr;
-            FD_TRY(sparse_launch(si, i, nsrc > 0, nrec > 0, s));
+            if (overlap) {
+                FD_TRY(side.fork(s));
+                FD_TRY(sparse_launch(si, i, false, true, side.get()));
+            }
+            if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 0), s));
+            FD_TRY(acoustic_launch(plan, ai, s));
+            if (!via_counter && trace_level() >= 2) FD_STAGE(s, "acoustic_step kernel");
+            if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 1), s));
+            FD_TRY(sparse_launch(si, i, nsrc > 0, !overlap && nrec > 0, s));
             if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 2), s));
+            if (overlap) FD_TRY(side.join(s));
             return FD_OK;
         };
         FD_TRY(run_time_loop(nsteps, s, counter, graphs, step));
@@ -690,7 +704,7 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
 
     TtiPlan tplan;
     FD_TRY(tti_plan(R, L, nshots, wave, tmp, bcoef, &tplan, stag ? 1 : 0,
-                    two_pass ? kTtiTwoPass : kTtiRecompute));
+                    two_pass ? kTtiTwoPass : kTtiRecompute, g_tti_config[R]));
     TtiArgs a;
     memset(&a, 0, sizeof(a));
     a.wave = wave;
@@ -1251,6 +1265,21 @@ fd_status fd_stats_reset(void) { return fdsweep::stats_reset(); }
 fd_status fd_stats_get(const char *family, double *total_ms, int64_t *launches,
                        double *points_per_launch) {
     return fdsweep::stats_get(family, total_ms, launches, points_per_launch);
+}
+
+fd_status fd_set_tti_config(int so, int config) {
+    fdsweep::clear_error();
+    if (!fdsweep::valid_so(so)) return fdsweep::set_error(FD_ERR_SO, "space order %d", so);
+    const int R = so / 2;
+    if (config < -1 || config >= fdsweep::tti_num_configs(R))
+        return fdsweep::set_error(FD_ERR_ARG, "TTI configuration %d out of range for so = %d",
+                                  config, so);
+    fdsweep::g_tti_config[R] = config;
+    return FD_OK;
+}
+
+int fd_num_tti_configs(int so) {
+    return fdsweep::valid_so(so) ? fdsweep::tti_num_configs(so / 2) : 0;
 }
 
 fd_status fd_set_time_tiling(int so, int mode) {

@@ -210,6 +210,7 @@ struct TtiPlan {
     int radius = 0;
     int stag = 0;    // 0: centred first derivatives, 1: staggered (D+ inner, D- outer)
     int scheme = kTtiTwoPass;
+    int config = 0;  // launch configuration of the two passes (tti_num_configs)
     CUtensorMap map_wint, map_whalo;          // p/r buffers: interior, x+y halo boxes
     CUtensorMap map_tint, map_tx, map_ty;     // temporaries: interior, x-halo, y-halo
     CUtensorMap map_cint;                     // b, a, s, n_x, n_y, n_z: interior box
@@ -223,7 +224,9 @@ struct TtiPlan {
 // differentiates them again; kTtiRecompute: one kernel recomputes the inner
 // derivatives at every outer stencil point (no temporaries; tmp unused).
 fd_status tti_plan(int radius, const WaveLayout &L, int nshots, float *wave, float *tmp,
-                   const float *coef, TtiPlan *plan, int stag = 0, int scheme = kTtiTwoPass);
+                   const float *coef, TtiPlan *plan, int stag = 0, int scheme = kTtiTwoPass,
+                   int config = 0);
+int tti_num_configs(int radius);
 fd_status tti_launch(const TtiPlan &plan, const TtiArgs &a, cudaStream_t stream,
                      cudaEvent_t *ev /* 3 events or null */);
 

@@ -251,6 +251,38 @@ fd_status CallStream::begin(cudaStream_t caller) {
     return FD_OK;
 }
 
+SideLane::~SideLane() {
+    if (f_) cudaEventDestroy(f_);
+    if (j_) cudaEventDestroy(j_);
+}
+
+fd_status SideLane::begin() {
+    thread_local cudaStream_t own = nullptr;
+    thread_local int own_dev = -1;
+    int dev = 0;
+    FD_CUDA_TRY(cudaGetDevice(&dev));
+    if (!own || own_dev != dev) {
+        FD_CUDA_TRY(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+        own_dev = dev;
+    }
+    s_ = own;
+    FD_CUDA_TRY(cudaEventCreateWithFlags(&f_, cudaEventDisableTiming));
+    FD_CUDA_TRY(cudaEventCreateWithFlags(&j_, cudaEventDisableTiming));
+    return FD_OK;
+}
+
+fd_status SideLane::fork(cudaStream_t from) {
+    FD_CUDA_TRY(cudaEventRecord(f_, from));
+    FD_CUDA_TRY(cudaStreamWaitEvent(s_, f_, 0));
+    return FD_OK;
+}
+
+fd_status SideLane::join(cudaStream_t into) {
+    FD_CUDA_TRY(cudaEventRecord(j_, s_));
+    FD_CUDA_TRY(cudaStreamWaitEvent(into, j_, 0));
+    return FD_OK;
+}
+
 fd_status CallStream::finish() {
     FD_CUDA_TRY(cudaEventRecord(done_, s_));
     FD_CUDA_TRY(cudaStreamWaitEvent(caller_, done_, 0));

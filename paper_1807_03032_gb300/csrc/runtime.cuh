@@ -66,4 +66,21 @@ class CallStream {
     cudaEvent_t done_ = nullptr;
 };
 
+// A second (thread-local, non-blocking) stream for work that may overlap the
+// call stream's kernels, forked from and joined back into it with events, so
+// that the dependencies are also captured when the call stream is being
+// recorded into a CUDA graph.
+class SideLane {
+  public:
+    ~SideLane();
+    fd_status begin();
+    cudaStream_t get() const { return s_; }
+    fd_status fork(cudaStream_t from);  // side waits for the work queued on `from`
+    fd_status join(cudaStream_t into);  // `into` waits for the work queued on side
+
+  private:
+    cudaStream_t s_ = nullptr;
+    cudaEvent_t f_ = nullptr, j_ = nullptr;
+};
+
 }  // namespace fdsweep

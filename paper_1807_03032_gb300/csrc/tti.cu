@@ -160,7 +160,7 @@ __device__ __forceinline__ Ring ring_init(unsigned char *raw, size_t stage_float
 
 // ---------------------------------------------------------------- pass 1
 
-template <int R, int TX, int TY, int D, int KIND>
+template <int R, int TX, int TY, int D, int KIND, int U>
 __global__ void __launch_bounds__(2 * TX * TY)
     tti_pass1_kernel(const __grid_constant__ CUtensorMap map_wint,
                      const __grid_constant__ CUtensorMap map_whalo,
@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(2 * TX * TY)
 #pragma unroll
     for (int i = 0; i < 2 * R; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     bool failed = false;
+#pragma unroll U
     for (int j = 0; j < nplanes; ++j) {
         if (tid == 0 && j + D < nplanes && !failed && !issue(j + D)) {
             failed = true;
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(2 * TX * TY)
 
 // ---------------------------------------------------------------- pass 2
 
-template <int R, int TX, int TY, int D, int KIND>
+template <int R, int TX, int TY, int D, int KIND, int U>
 __global__ void __launch_bounds__(2 * TX * TY)
     tti_pass2_kernel(const __grid_constant__ CUtensorMap map_tint,
                      const __grid_constant__ CUtensorMap map_tx,
@@ -349,6 +350,7 @@ __global__ void __launch_bounds__(2 * TX * TY)
 #pragma unroll
     for (int i = 0; i < 2 * R; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     bool failed = false;
+#pragma unroll U
     for (int j = 0; j < nplanes; ++j) {
         if (tid == 0 && j + D < nplanes && !failed && !issue(j + D)) {
             failed = true;
@@ -510,18 +512,20 @@ __global__ void __launch_bounds__(kRecBX *kRecBY) tti_recompute_kernel(const Tti
 
 constexpr int kTX = 16, kTY = 8;  // 64 x 8 tile, two groups of 128 threads
 
-// Prefetch depth per pass: pass 2 stages carry eleven tiles, so for the wide
-// stencils one slot less keeps two CTAs per SM.
-template <int R, int STAG>
+// Launch configurations of the two passes: prefetch depths D1, D2 and the
+// unroll U of the plane loop (the pending z-outputs rotate by one register
+// per plane; unrolling turns the moves into renaming).  Pass 2 stages carry
+// eleven tiles, so a shallower ring keeps more CTAs per SM.
+template <int R, int STAG, int D1_, int D2_, int U_>
 struct TtiKernels {
-    static constexpr int D1 = 2;
-    static constexpr int D2 = R >= 6 ? 1 : 2;
+    static constexpr int D1 = D1_;
+    static constexpr int D2 = D2_;
     static constexpr int K1 = STAG ? 1 : 0;   // inner derivative: D+ or centred
     static constexpr int K2 = STAG ? -1 : 0;  // outer derivative: D- or centred
     using C1 = TtiCfg<R, kTX, kTY, D1>;
     using C2 = TtiCfg<R, kTX, kTY, D2>;
-    static const void *p1() { return (const void *)&tti_pass1_kernel<R, kTX, kTY, D1, K1>; }
-    static const void *p2() { return (const void *)&tti_pass2_kernel<R, kTX, kTY, D2, K2>; }
+    static const void *p1() { return (const void *)&tti_pass1_kernel<R, kTX, kTY, D1, K1, U_>; }
+    static const void *p2() { return (const void *)&tti_pass2_kernel<R, kTX, kTY, D2, K2, U_>; }
     static const void *rc() { return (const void *)&tti_recompute_kernel<R, K1, K2>; }
 };
 
@@ -531,9 +535,9 @@ struct TtiInfo {
     int bx, by, pw, ph, threads;
 };
 
-template <int R, int STAG>
+template <int R, int STAG, int D1, int D2, int U>
 TtiInfo info_r() {
-    using K = TtiKernels<R, STAG>;
+    using K = TtiKernels<R, STAG, D1, D2, U>;
     using C1 = typename K::C1;
     using C2 = typename K::C2;
     static_assert(C1::BX == C2::BX && C1::BY == C2::BY && C1::THREADS == C2::THREADS, "tiles");
@@ -541,32 +545,61 @@ TtiInfo info_r() {
                    C1::THREADS};
 }
 
-template <int STAG>
-bool tti_info_s(int radius, TtiInfo *out) {
-    switch (radius) {
-        case 1: *out = info_r<1, STAG>(); return true;
-        case 2: *out = info_r<2, STAG>(); return true;
-        case 4: *out = info_r<4, STAG>(); return true;
-        case 6: *out = info_r<6, STAG>(); return true;
-        case 8: *out = info_r<8, STAG>(); return true;
+// Configuration tables (index 0 the default, measured on GB300 at 512^3);
+// the staggered reading is compiled in its default configuration only.
+template <int R, int STAG>
+bool tti_info_r(int config, TtiInfo *out) {
+    constexpr int D2d = R >= 6 ? 1 : 2;
+    if (STAG) {
+        *out = info_r<R, STAG, 2, D2d, 1>();
+        return true;
+    }
+    switch (config) {
+        case 0: *out = info_r<R, 0, 2, D2d, 1>(); return true;
+        case 1: *out = info_r<R, 0, 2, D2d, 4>(); return true;
+        case 2: *out = info_r<R, 0, 2, 1, 4>(); return true;
+        case 3: *out = info_r<R, 0, 3, 2, 4>(); return true;
+        case 4: *out = info_r<R, 0, 1, 1, 4>(); return true;
+        case 5: *out = info_r<R, 0, 3, 1, 1>(); return true;
         default: return false;
     }
 }
 
-bool tti_info(int radius, int stag, TtiInfo *out) {
-    return stag ? tti_info_s<1>(radius, out) : tti_info_s<0>(radius, out);
+constexpr int kTtiConfigs = 6;
+
+template <int STAG>
+bool tti_info_s(int radius, int config, TtiInfo *out) {
+    switch (radius) {
+        case 1: return tti_info_r<1, STAG>(config, out);
+        case 2: return tti_info_r<2, STAG>(config, out);
+        case 4: return tti_info_r<4, STAG>(config, out);
+        case 6: return tti_info_r<6, STAG>(config, out);
+        case 8: return tti_info_r<8, STAG>(config, out);
+        default: return false;
+    }
+}
+
+bool tti_info(int radius, int stag, int config, TtiInfo *out) {
+    if (config < 0 || config >= kTtiConfigs) config = 0;
+    return stag ? tti_info_s<1>(radius, 0, out) : tti_info_s<0>(radius, config, out);
 }
 
 }  // namespace
 
-fd_status tti_plan(int radius, const WaveLayout &L, int nshots, float *wave, float *tmp,
-                   const float *coef, TtiPlan *plan, int stag, int scheme) {
+int tti_num_configs(int radius) {
     TtiInfo in;
-    if (!tti_info(radius, stag, &in))
+    return tti_info(radius, 0, 0, &in) ? kTtiConfigs : 0;
+}
+
+fd_status tti_plan(int radius, const WaveLayout &L, int nshots, float *wave, float *tmp,
+                   const float *coef, TtiPlan *plan, int stag, int scheme, int config) {
+    TtiInfo in;
+    if (!tti_info(radius, stag, config, &in))
         return set_error(FD_ERR_SO, "no TTI kernel for radius %d", radius);
     plan->radius = radius;
     plan->stag = stag ? 1 : 0;
     plan->scheme = scheme;
+    plan->config = config < 0 || config >= kTtiConfigs ? 0 : config;
     if (scheme == kTtiRecompute) {
         if ((int64_t)nshots * L.nz > 65535)
             return set_error(FD_ERR_ARG, "grid too large for the TTI recompute launch");
@@ -620,7 +653,8 @@ fd_status tti_plan(int radius, const WaveLayout &L, int nshots, float *wave, flo
 fd_status tti_launch(const TtiPlan &plan, const TtiArgs &a, cudaStream_t stream,
                      cudaEvent_t *ev) {
     TtiInfo in;
-    if (!tti_info(plan.radius, plan.stag, &in)) return set_error(FD_ERR_SO, "bad TTI plan");
+    if (!tti_info(plan.radius, plan.stag, plan.config, &in))
+        return set_error(FD_ERR_SO, "bad TTI plan");
     int zchunk = plan.zchunk, nzc = plan.nzc;
     if (ev) FD_CUDA_TRY(cudaEventRecord(ev[0], stream));
     if (plan.scheme == kTtiRecompute) {
