@@ -194,6 +194,42 @@ struct StagedOut {
     }
 };
 
+// Copies the finished time rows [done, upto) of traces [nshots][nt][nrec]
+// staged on the device back to host memory on a copy stream while the time
+// loop continues (the copy waits for the rows' producer on the call stream).
+struct TraceStreamer {
+    StagedOut *out = nullptr;
+    int nshots = 0, nt = 0, nrec = 0;
+    int done = 0;
+    SideLane lane{1};
+    bool active() const { return out && out->host && nrec > 0; }
+    fd_status begin(StagedOut *o, int ns, int t, int nr) {
+        out = o;
+        nshots = ns;
+        nt = t;
+        nrec = nr;
+        done = 0;
+        return active() ? lane.begin() : FD_OK;
+    }
+    fd_status upto(int rows, cudaStream_t s) {
+        if (!active() || rows <= done) return FD_OK;
+        FD_TRY(lane.fork(s));
+        const size_t pitch = (size_t)nt * nrec * sizeof(float);
+        FD_CUDA_TRY(cudaMemcpy2DAsync(out->user + (size_t)done * nrec, pitch,
+                                      out->dev + (size_t)done * nrec, pitch,
+                                      (size_t)(rows - done) * nrec * sizeof(float), nshots,
+                                      cudaMemcpyDeviceToHost, lane.get()));
+        done = rows;
+        return FD_OK;
+    }
+    // the remaining rows, then the call stream waits for every copy
+    fd_status finish(cudaStream_t s) {
+        if (!active()) return FD_OK;
+        FD_TRY(upto(nt, s));
+        return lane.join(s);
+    }
+};
+
 // Host copy of the device MediumStats after a synchronisation.
 fd_status read_stats(const MediumStats *dev, MediumStats *host, cudaStream_t s) {
     FD_CUDA_TRY(cudaMemcpyAsync(host, dev, sizeof(MediumStats), cudaMemcpyDeviceToHost, s));
@@ -239,9 +275,16 @@ fd_status copy_field_out(float *dst_dense, const float *src_buf, const WaveLayou
 
 // Runs `nsteps` steps.  step(i, parity, use_counter) enqueues one step; with
 // use_counter the sparse kernel's time index is *counter + i, otherwise i.
-template <class StepFn>
+struct NoProgress {
+    fd_status operator()(int) const { return FD_OK; }
+};
+
+// `progress(n)` is called (on the host, after enqueueing) whenever the first n
+// units are enqueued: after every graph replay and every kGraphChunk direct
+// units, and at the end.
+template <class StepFn, class ProgressFn = NoProgress>
 fd_status run_time_loop(int nsteps, cudaStream_t s, int *counter, bool allow_graph,
-                        StepFn step) {
+                        StepFn step, ProgressFn progress = ProgressFn()) {
     int n = 0;
     if (allow_graph && nsteps >= 2 * kGraphChunk) {
         FD_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
@@ -263,20 +306,26 @@ fd_status run_time_loop(int nsteps, cudaStream_t s, int *counter, bool allow_gra
             cudaGraphDestroy(graph);
             FD_CUDA_TRY(e);
             const int reps = nsteps / kGraphChunk;
-            for (int r = 0; r < reps; ++r) {
+            fd_status pst = FD_OK;
+            for (int r = 0; r < reps && pst == FD_OK; ++r) {
                 e = cudaGraphLaunch(exec, s);
                 if (e != cudaSuccess) break;
+                pst = progress((r + 1) * kGraphChunk);
             }
             cudaGraphExecDestroy(exec);  // released once the queued launches complete
             add_launches(per_graph * reps);
             FD_CUDA_TRY(e);
+            FD_TRY(pst);
             n = reps * kGraphChunk;
         } else {
             cudaGetLastError();
         }
     }
-    for (; n < nsteps; ++n) FD_TRY(step(n, n & 1, false));
-    return FD_OK;
+    for (; n < nsteps; ++n) {
+        FD_TRY(step(n, n & 1, false));
+        if ((n + 1) % kGraphChunk == 0 && n + 1 < nsteps) FD_TRY(progress(n + 1));
+    }
+    return progress(nsteps);
 }
 
 // Events bracketing the kernels of every step when statistics are on.
@@ -365,6 +414,8 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     srec.plan(ws, rec_out, (size_t)nshots * nt * nrec);
     FD_TRY(ws.allocate(s));
     FD_STAGE(s, "acoustic: workspace allocated");
+    TraceStreamer traces;  // host traces: copied back while the loop runs
+    FD_TRY(traces.begin(&srec, nshots, nt, nrec));
     for (Staged *st : {&sm, &sdamp, &ssxyz, &swav, &srxyz}) FD_TRY(st->place(s));
     FD_STAGE(s, "acoustic: inputs staged");
 
@@ -484,7 +535,8 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
             if (overlap) FD_TRY(side.join(s));
             return FD_OK;
         };
-        FD_TRY(run_time_loop(nsteps, s, counter, graphs, step));
+        FD_TRY(run_time_loop(nsteps, s, counter, graphs, step,
+                             [&](int n) { return traces.upto(n, s); }));
     } else {
         // Two steps per launch over four levels per shot: pair i (parity par)
         // reads u^n, u^{n-1} from levels (0, 1) or (3, 2) and writes u^{n+1},
@@ -534,7 +586,8 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
             if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 2), s));
             return FD_OK;
         };
-        FD_TRY(run_time_loop(npairs, s, counter, graphs, pair));
+        FD_TRY(run_time_loop(npairs, s, counter, graphs, pair,
+                             [&](int np) { return traces.upto(2 * np, s); }));
         last = (npairs & 1) ? 3 : 0;
         prev_of_last = (npairs & 1) ? 2 : 1;
         if (nsteps & 1) {  // one single step to finish, in place
@@ -576,7 +629,10 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
                                   L, s));
         }
     }
-    FD_TRY(srec.copy_back(s));
+    if (traces.active())
+        FD_TRY(traces.finish(s));
+    else
+        FD_TRY(srec.copy_back(s));
     FD_TRY(read_stats(dstats, &hs, s));
     if (timing && nsteps > 0) {
         double kms = 0.0, sms = 0.0;

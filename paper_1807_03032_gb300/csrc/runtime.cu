@@ -257,15 +257,16 @@ SideLane::~SideLane() {
 }
 
 fd_status SideLane::begin() {
-    thread_local cudaStream_t own = nullptr;
-    thread_local int own_dev = -1;
+    thread_local cudaStream_t own[2] = {nullptr, nullptr};
+    thread_local int own_dev[2] = {-1, -1};
+    const int l = lane_ ? 1 : 0;
     int dev = 0;
     FD_CUDA_TRY(cudaGetDevice(&dev));
-    if (!own || own_dev != dev) {
-        FD_CUDA_TRY(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
-        own_dev = dev;
+    if (!own[l] || own_dev[l] != dev) {
+        FD_CUDA_TRY(cudaStreamCreateWithFlags(&own[l], cudaStreamNonBlocking));
+        own_dev[l] = dev;
     }
-    s_ = own;
+    s_ = own[l];
     FD_CUDA_TRY(cudaEventCreateWithFlags(&f_, cudaEventDisableTiming));
     FD_CUDA_TRY(cudaEventCreateWithFlags(&j_, cudaEventDisableTiming));
     return FD_OK;

@@ -72,6 +72,7 @@ class CallStream {
 // recorded into a CUDA graph.
 class SideLane {
   public:
+    explicit SideLane(int lane = 0) : lane_(lane) {}
     ~SideLane();
     fd_status begin();
     cudaStream_t get() const { return s_; }
@@ -79,6 +80,7 @@ class SideLane {
     fd_status join(cudaStream_t into);  // `into` waits for the work queued on side
 
   private:
+    int lane_ = 0;  // 0 or 1: distinct thread-local streams
     cudaStream_t s_ = nullptr;
     cudaEvent_t f_ = nullptr, j_ = nullptr;
 };
