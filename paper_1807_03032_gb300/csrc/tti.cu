@@ -259,9 +259,11 @@ __global__ void __launch_bounds__(2 * TX * TY)
             }
             if (ok) {
                 const int64_t off = (int64_t)zs * a.L.plane + (int64_t)gy * a.L.nxp + gx;
-                *reinterpret_cast<float4 *>(out + off) = o0;
-                *reinterpret_cast<float4 *>(out + a.L.vol + off) = o1;
-                *reinterpret_cast<float4 *>(out + 2 * a.L.vol + off) = o2;
+                // streaming stores: the temporaries are read once, by pass 2,
+                // and must not push the p/r halo planes out of L2 meanwhile
+                __stcs(reinterpret_cast<float4 *>(out + off), o0);
+                __stcs(reinterpret_cast<float4 *>(out + a.L.vol + off), o1);
+                __stcs(reinterpret_cast<float4 *>(out + 2 * a.L.vol + off), o2);
             }
         }
         __syncwarp();
