@@ -74,9 +74,17 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the sources the acoustic stencil kernels are built from (for
+    kernels.cuh, only its acoustic section), so that a recorded ncu traffic
+    figure is reported only for the kernel version it was measured on."""
     h = hashlib.sha256()
-    for f in ("acoustic.cu", "acoustic2.cu", "f32x2.cuh", "kernels.cuh", "common.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1807_03032_gb300", "csrc", f), "rb").read())
+    csrc = os.path.join(ROOT, "paper_1807_03032_gb300", "csrc")
+    for f in ("acoustic.cu", "acoustic2.cu", "f32x2.cuh", "common.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    k = open(os.path.join(csrc, "kernels.cuh"), "rb").read()
+    a = k.find(b"// ---------------------------------------------------------------- acoustic K1")
+    b = k.find(b"// ---------------------------------------------------------------- sparse K3/K4")
+    h.update(k[a:b] if 0 <= a < b else k)
     return h.hexdigest()[:16]
 
 
@@ -464,8 +472,9 @@ def run_tti(args, fd, _native, dev, stream, peak):
 
 def run_tti_ablation(args, fd, _native, g, w, m, e, d, th, ph, sx, sw, rx, dd, per_so):
     """TTI variants on the same workload, per-step kernel time over a short
-    run: temporaries (two passes) vs recomputed inner derivatives (one pass),
-    centred vs staggered first derivatives.  FMA counts per point per step
+    run: temporaries in HBM (two passes), temporaries in shared memory (one
+    fused pass, so <= 8) and recomputed inner derivatives (one pass), centred
+    vs staggered first derivatives.  FMA counts per point per step
     are those of the kernel sources (R = so/2): two passes 24R + 30, recompute
     72R^2 + 60R (the inner gradient of p and r at each of the 6R outer taps)."""
     import torch
@@ -478,9 +487,12 @@ def run_tti_ablation(args, fd, _native, g, w, m, e, d, th, ph, sx, sw, rx, dd, p
         R = so // 2
         row = {"two_pass_centred_ms": per_so[str(so)]["step_kernel_ms"],
                "fma_per_point": {"two_pass": 24 * R + 30, "recompute": 72 * R * R + 60 * R}}
-        for deriv, scheme, key in (("staggered", "two_pass", "two_pass_staggered_ms"),
-                                   ("centred", "recompute", "recompute_centred_ms"),
-                                   ("staggered", "recompute", "recompute_staggered_ms")):
+        variants = [("staggered", "two_pass", "two_pass_staggered_ms"),
+                    ("centred", "recompute", "recompute_centred_ms"),
+                    ("staggered", "recompute", "recompute_staggered_ms")]
+        if so <= 8:  # temporaries in shared memory: radii up to 4
+            variants.append(("centred", "fused", "fused_centred_ms"))
+        for deriv, scheme, key in variants:
             fd.tti_forward(g, so, w.dt, 4, m, e, d, th, ph, sx, sw_ab[:, :4].contiguous(), rx,
                            damp=dd, rec_out=rec[:, :4].contiguous(), return_final=False,
                            deriv=deriv, scheme=scheme)
@@ -494,11 +506,14 @@ def run_tti_ablation(args, fd, _native, g, w, m, e, d, th, ph, sx, sw, rx, dd, p
                 p2 = _native.stats_get("tti_pass2")
                 kms = (p1[0] + p2[0]) / max(p1[1], 1)
             else:
-                pr = _native.stats_get("tti_recompute")
+                pr = _native.stats_get("tti_" + scheme)
                 kms = pr[0] / max(pr[1], 1)
             _native.stats_enable(False)
             row[key] = round(kms, 4)
         row["recompute_over_two_pass"] = round(row["recompute_centred_ms"] /
+                                               row["two_pass_centred_ms"], 2)
+        if "fused_centred_ms" in row:
+            row["fused_over_two_pass"] = round(row["fused_centred_ms"] /
                                                row["two_pass_centred_ms"], 2)
         res[str(so)] = row
         log(f"[bench] TTI ablation so={so}: {row}")
