@@ -456,14 +456,18 @@ def run_tti(args, fd, _native, dev, stream, peak):
         ms = e0.elapsed_time(e1)
         p1 = _native.stats_get("tti_pass1")
         p2 = _native.stats_get("tti_pass2")
+        pf = _native.stats_get("tti_fused")
         _native.stats_enable(False)
-        kms = (p1[0] + p2[0]) / max(p1[1], 1)
-        gb = BYTES_PER_POINT_TTI * p1[2] / (kms * 1e-3) / 1e9
-        out["per_so"][str(so)] = {"gpts": round(pts / (ms * 1e-3) / 1e9, 2),
-                                  "step_kernel_ms": round(kms, 4),
-                                  "pass1_ms": round(p1[0] / max(p1[1], 1), 4),
-                                  "pass2_ms": round(p2[0] / max(p2[1], 1), 4),
-                                  "hbm_frac_44B": round(gb / peak, 4)}
+        steps = max(p1[1], pf[1], 1)
+        kms = (p1[0] + p2[0] + pf[0]) / steps
+        npts = max(p1[2], pf[2])
+        gb = BYTES_PER_POINT_TTI * npts / (kms * 1e-3) / 1e9
+        row = {"gpts": round(pts / (ms * 1e-3) / 1e9, 2), "step_kernel_ms": round(kms, 4),
+               "kernel_gpts": round(npts / (kms * 1e-3) / 1e9, 2),
+               "scheme": "fused" if pf[1] else "two_pass", "hbm_frac_44B": round(gb / peak, 4)}
+        if p1[1]:
+            row.update({"pass1_ms": round(p1[0] / p1[1], 4), "pass2_ms": round(p2[0] / p2[1], 4)})
+        out["per_so"][str(so)] = row
     if not args.no_tti_ablation:
         out["ablation"] = run_tti_ablation(args, fd, _native, g, w, m, e, d, th, ph, sx, sw, rx,
                                            dd, out["per_so"])
@@ -485,11 +489,14 @@ def run_tti_ablation(args, fd, _native, g, w, m, e, d, th, ph, sx, sw, rx, dd, p
            "two_pass_centred from the main TTI run"}
     for so in args.so:
         R = so // 2
-        row = {"two_pass_centred_ms": per_so[str(so)]["step_kernel_ms"],
-               "fma_per_point": {"two_pass": 24 * R + 30, "recompute": 72 * R * R + 60 * R}}
+        row = {"fma_per_point": {"two_pass": 24 * R + 30, "recompute": 72 * R * R + 60 * R}}
+        if per_so[str(so)]["scheme"] == "two_pass":
+            row["two_pass_centred_ms"] = per_so[str(so)]["step_kernel_ms"]
         variants = [("staggered", "two_pass", "two_pass_staggered_ms"),
                     ("centred", "recompute", "recompute_centred_ms"),
                     ("staggered", "recompute", "recompute_staggered_ms")]
+        if "two_pass_centred_ms" not in row:
+            variants.insert(0, ("centred", "two_pass", "two_pass_centred_ms"))
         if so <= 8:  # temporaries in shared memory: radii up to 4
             variants.append(("centred", "fused", "fused_centred_ms"))
         for deriv, scheme, key in variants:

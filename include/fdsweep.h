@@ -122,6 +122,9 @@ fd_status acoustic_forward(const fd_grid *grid, int so, double dt, int nt, int n
  *   p_final, r_final NULL or [nshots][2][nz][ny][nx].
  *   rec_out   [nshots][nt][nrec] samples of p.
  *   Other arguments as for acoustic_forward.
+ * The kernels: one fused kernel per step with the first-derivative
+ * temporaries in shared memory for so <= 4, two passes with the temporaries
+ * in device memory above (see tti_forward_opts).
  */
 fd_status tti_forward(const fd_grid *grid, int so, double dt, int nt, int nshots, const float *m,
                       const float *damp, const float *epsilon, const float *delta,
@@ -147,19 +150,24 @@ fd_status tti_forward(const fd_grid *grid, int so, double dt, int nt, int nshots
  *                   stability bound uses the staggered symbol.
  *   opts->receiver  FD_TTI_REC_P: receivers record p; FD_TTI_REC_MEAN: they
  *                   record (p + r)/2.
- *   opts->scheme    FD_TTI_TWO_PASS: six first-derivative temporaries per
- *                   point are written once and differentiated again (the
- *                   default, linear work in so); FD_TTI_RECOMPUTE: no
+ *   opts->scheme    FD_TTI_AUTO (what tti_forward uses): FD_TTI_FUSED for
+ *                   so <= 4, FD_TTI_TWO_PASS otherwise (the faster on GB300);
+ *                   FD_TTI_TWO_PASS: six first-derivative temporaries per
+ *                   point are written to device memory once and
+ *                   differentiated again by a second kernel (the default,
+ *                   linear work in so); FD_TTI_FUSED: one kernel, the
+ *                   temporaries of each plane kept in shared memory
+ *                   (so <= 8, else FD_ERR_ARG); FD_TTI_RECOMPUTE: no
  *                   temporaries, the inner derivatives are recomputed at
- *                   every outer stencil point (work quadratic in so; one
- *                   kernel per step; uses 6 fewer fields of device memory).
- *   opts            NULL selects the tti_forward defaults.  Out-of-range
- *                   values return FD_ERR_ARG.
+ *                   every outer stencil point (work quadratic in so).  The
+ *                   last two use 6 fewer fields of device memory.
+ *   opts            NULL selects the tti_forward defaults (centred, p,
+ *                   automatic scheme).  Out-of-range values return FD_ERR_ARG.
  * Other arguments, ownership and errors as for tti_forward.
  */
 enum { FD_TTI_CENTRED = 0, FD_TTI_STAGGERED = 1 };
 enum { FD_TTI_REC_P = 0, FD_TTI_REC_MEAN = 1 };
-enum { FD_TTI_TWO_PASS = 0, FD_TTI_RECOMPUTE = 1 };
+enum { FD_TTI_AUTO = -1, FD_TTI_TWO_PASS = 0, FD_TTI_RECOMPUTE = 1, FD_TTI_FUSED = 2 };
 typedef struct {
     int32_t deriv;
     int32_t receiver;
@@ -312,8 +320,8 @@ const char *fd_version(void);
  * times are accumulated per kernel family when the call completes.
  * Families: "acoustic_step", "acoustic_step2" (two time steps per launch, see
  * fd_set_time_tiling; points_per_launch counts the points of one step),
- * "tti_pass1", "tti_pass2", "tti_recompute" (the one-kernel TTI scheme of
- * tti_forward_opts), "sparse".
+ * "tti_pass1", "tti_pass2", "tti_recompute", "tti_fused" (the one-kernel TTI
+ * schemes of tti_forward_opts), "sparse".
  * fd_stats_get returns FD_ERR_ARG for an unknown family.
  */
 fd_status fd_stats_enable(int on);

@@ -121,11 +121,12 @@ def acoustic_forward(grid, so, dt, nt, m, src_xyz, src_wav, rec_xyz, damp=None, 
 def tti_forward(grid, so, dt, nt, m, eps, delta, theta, phi, src_xyz, src_wav, rec_xyz,
                 damp=None, p_init=None, r_init=None, rec_out=None, p_final=None, r_final=None,
                 return_final=True, stream=None, deriv="centred", receiver="p",
-                scheme="two_pass"):
+                scheme="auto"):
     """TTI forward model (C ABI ``tti_forward``, or ``tti_forward_opts`` for the
     alternative readings).  deriv: "centred" | "staggered"; receiver: "p" |
-    "mean" ((p + r)/2); scheme: "two_pass" (temporaries) | "recompute".
-    Returns (rec, p_final, r_final)."""
+    "mean" ((p + r)/2); scheme: "auto" | "fused" (temporaries in shared
+    memory, so <= 8) | "two_pass" (temporaries in device memory) |
+    "recompute" (no temporaries).  Returns (rec, p_final, r_final)."""
     g = _as_grid(grid)
     nshots, nsrc = int(src_xyz.shape[0]), int(src_xyz.shape[1])
     nrec = int(rec_xyz.shape[1])
@@ -145,7 +146,7 @@ def tti_forward(grid, so, dt, nt, m, eps, delta, theta, phi, src_xyz, src_wav, r
             _ptr(rec_xyz, "rec_xyz"), _ptr(rec_out, "rec_out"), _ptr(p_init, "p_init"),
             _ptr(r_init, "r_init"), _ptr(p_final, "p_final"), _ptr(r_final, "r_final"))
     stream_ptr = _stream_for(m, rec_out, stream=stream)
-    if (deriv, receiver, scheme) == ("centred", "p", "two_pass"):
+    if (deriv, receiver, scheme) == ("centred", "p", "auto"):
         st = lib.tti_forward(*args, stream_ptr)
     else:
         opts = _native.FdTtiOptions(_native.TTI_DERIV[deriv], _native.TTI_RECEIVER[receiver],

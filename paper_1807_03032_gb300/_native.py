@@ -48,7 +48,7 @@ class FdTtiOptions(ctypes.Structure):
 
 TTI_DERIV = {"centred": 0, "staggered": 1}
 TTI_RECEIVER = {"p": 0, "mean": 1}
-TTI_SCHEME = {"two_pass": 0, "recompute": 1}
+TTI_SCHEME = {"auto": -1, "two_pass": 0, "recompute": 1, "fused": 2}
 
 
 class FdError(RuntimeError):

@@ -670,15 +670,24 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
                            rec_out));
     if (!eps || !delta || !theta || !phi)
         return set_error(FD_ERR_ARG, "tti_forward: epsilon, delta, theta and phi are required");
-    fd_tti_options op = {FD_TTI_CENTRED, FD_TTI_REC_P, FD_TTI_TWO_PASS};
+    fd_tti_options op = {FD_TTI_CENTRED, FD_TTI_REC_P, FD_TTI_AUTO};
     if (opts) op = *opts;
     if ((op.deriv != FD_TTI_CENTRED && op.deriv != FD_TTI_STAGGERED) ||
         (op.receiver != FD_TTI_REC_P && op.receiver != FD_TTI_REC_MEAN) ||
-        (op.scheme != FD_TTI_TWO_PASS && op.scheme != FD_TTI_RECOMPUTE))
+        (op.scheme != FD_TTI_AUTO && op.scheme != FD_TTI_TWO_PASS &&
+         op.scheme != FD_TTI_RECOMPUTE && op.scheme != FD_TTI_FUSED))
         return set_error(FD_ERR_ARG, "tti_forward: options (%d, %d, %d) out of range", op.deriv,
                          op.receiver, op.scheme);
+    // automatic: the fused kernel where it was measured faster (so <= 4:
+    // 2.02 against 2.41 ms per 512^3 step at so 4), two passes otherwise
+    if (op.scheme == FD_TTI_AUTO)
+        op.scheme = (so <= 4 && tti_fused_supported(so / 2)) ? FD_TTI_FUSED : FD_TTI_TWO_PASS;
+    if (op.scheme == FD_TTI_FUSED && !tti_fused_supported(so / 2))
+        return set_error(FD_ERR_ARG, "tti_forward: the fused scheme covers so <= 8 (so = %d)",
+                         so);
     const bool stag = op.deriv == FD_TTI_STAGGERED;
     const bool two_pass = op.scheme == FD_TTI_TWO_PASS;
+    const bool fused = op.scheme == FD_TTI_FUSED;
     const int R = so / 2;
     GridDerived gd = derive(grid, so);
     const WaveLayout &L = gd.L;
@@ -759,8 +768,11 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
     }
 
     TtiPlan tplan;
-    FD_TRY(tti_plan(R, L, nshots, wave, tmp, bcoef, &tplan, stag ? 1 : 0,
-                    two_pass ? kTtiTwoPass : kTtiRecompute, g_tti_config[R]));
+    if (fused)
+        FD_TRY(tti_fused_plan(R, stag ? 1 : 0, L, nshots, wave, bcoef, &tplan));
+    else
+        FD_TRY(tti_plan(R, L, nshots, wave, tmp, bcoef, &tplan, stag ? 1 : 0,
+                        two_pass ? kTtiTwoPass : kTtiRecompute, g_tti_config[R]));
     TtiArgs a;
     memset(&a, 0, sizeof(a));
     a.wave = wave;
@@ -873,7 +885,7 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
             stats_add("tti_pass1", t1, nsteps, (double)dense * nshots);
             stats_add("tti_pass2", t2, nsteps, (double)dense * nshots);
         } else {
-            stats_add("tti_recompute", t1, nsteps, (double)dense * nshots);
+            stats_add(fused ? "tti_fused" : "tti_recompute", t1, nsteps, (double)dense * nshots);
         }
         stats_add("sparse", ts, nsteps, (double)(nrec + 16 * nsrc) * nshots);
     }

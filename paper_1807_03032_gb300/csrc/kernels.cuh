@@ -204,7 +204,7 @@ struct TtiArgs {
     unsigned int *err;
 };
 
-enum TtiScheme { kTtiTwoPass = 0, kTtiRecompute = 1 };
+enum TtiScheme { kTtiTwoPass = 0, kTtiRecompute = 1, kTtiFused = 2 };
 
 struct TtiPlan {
     int radius = 0;
@@ -214,6 +214,7 @@ struct TtiPlan {
     CUtensorMap map_wint, map_whalo;          // p/r buffers: interior, x+y halo boxes
     CUtensorMap map_tint, map_tx, map_ty;     // temporaries: interior, x-halo, y-halo
     CUtensorMap map_cint;                     // b, a, s, n_x, n_y, n_z: interior box
+    CUtensorMap map_fbox, map_fnbox;          // fused scheme: p/r plane box, n box
     dim3 grid, block;
     size_t smem1 = 0, smem2 = 0;
     int zchunk = 0, nzc = 1;
@@ -227,6 +228,12 @@ fd_status tti_plan(int radius, const WaveLayout &L, int nshots, float *wave, flo
                    const float *coef, TtiPlan *plan, int stag = 0, int scheme = kTtiTwoPass,
                    int config = 0);
 int tti_num_configs(int radius);
+// Fused scheme (tti_fused.cu): one kernel per step, temporaries in shared
+// memory; radii 1, 2 and 4.
+bool tti_fused_supported(int radius);
+fd_status tti_fused_plan(int radius, int stag, const WaveLayout &L, int nshots, float *wave,
+                         const float *coef, TtiPlan *plan);
+fd_status tti_fused_launch(const TtiPlan &plan, const TtiArgs &a, cudaStream_t stream);
 fd_status tti_launch(const TtiPlan &plan, const TtiArgs &a, cudaStream_t stream,
                      cudaEvent_t *ev /* 3 events or null */);
 

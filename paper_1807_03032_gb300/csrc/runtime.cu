@@ -95,7 +95,7 @@ fd_status stats_get(const char *family, double *total_ms, int64_t *launches,
     if (!family) return set_error(FD_ERR_ARG, "fd_stats_get: null family");
     std::lock_guard<std::mutex> lk(g_stats_mu);
     static const char *known[] = {"acoustic_step", "acoustic_step2", "tti_pass1", "tti_pass2",
-                                  "tti_recompute", "sparse"};
+                                  "tti_recompute", "tti_fused", "sparse"};
     bool ok = false;
     for (const char *k : known) ok = ok || strcmp(k, family) == 0;
     if (!ok) return set_error(FD_ERR_ARG, "fd_stats_get: unknown family '%s'", family);

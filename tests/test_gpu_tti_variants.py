@@ -60,7 +60,41 @@ def test_recompute_scheme_parity(so, deriv):
     check(*run_pair(w, deriv=deriv, scheme="recompute"))
 
 
-@pytest.mark.parametrize("scheme", ["two_pass", "recompute"])
+@pytest.mark.parametrize("so", [2, 4])
+def test_two_pass_centred_small_orders(so):
+    """The two-pass scheme where the automatic choice is the fused one."""
+    w = workloads.tti_small(so=so, nt=60)
+    check(*run_pair(w, scheme="two_pass"))
+
+
+@pytest.mark.parametrize("so,deriv", [(2, "centred"), (4, "centred"), (4, "staggered"),
+                                      (8, "centred"), (8, "staggered")])
+def test_fused_scheme_parity(so, deriv):
+    """One kernel per step with the temporaries in shared memory."""
+    w = workloads.tti_small(so=so, nt=60)
+    check(*run_pair(w, deriv=deriv, scheme="fused"))
+
+
+@pytest.mark.parametrize("so", [4, 8])
+def test_fused_scheme_interior_and_chunks(so):
+    """80^3 (interior tiles away from every boundary, z split into chunks)."""
+    w = workloads.tti_small(so=so, nt=40, n=80)
+    check(*run_pair(w, scheme="fused"))
+
+
+def test_fused_scheme_rejects_wide_stencils():
+    torch = require_cuda()
+    import paper_1807_03032_gb300 as fd
+    from paper_1807_03032_gb300 import _native
+    w = workloads.tti_small(so=12, nt=4)
+    g = fd.Grid(w.shape, w.spacing, w.origin)
+    m, e, d, th, ph, sx, sw, rx = to_dev(torch, w.m, w.eps, w.delta, w.theta, w.phi, w.src_xyz,
+                                         w.src_wav, w.rec_xyz)
+    with pytest.raises(_native.FdError):
+        fd.tti_forward(g, 12, w.dt, w.nt, m, e, d, th, ph, sx, sw, rx, scheme="fused")
+
+
+@pytest.mark.parametrize("scheme", ["two_pass", "recompute", "fused"])
 def test_ragged_multishot_staggered_mean(scheme):
     """Ragged box, anisotropic spacing, two shots, random initial fields,
     theta over [0, pi] (n_z of either sign), staggered derivatives and mean
@@ -103,7 +137,7 @@ def test_options_out_of_range_rejected():
     rec = torch.empty((1, w.nt, w.rec_xyz.shape[1]), device="cuda")
     lib = _native.load()
     P = lambda t: ctypes.c_void_p(t.data_ptr())
-    for bad in ((2, 0, 0), (0, 5, 0), (0, 0, -1)):
+    for bad in ((2, 0, 0), (0, 5, 0), (0, 0, 7), (0, 0, -2)):
         opts = _native.FdTtiOptions(*bad)
         st = lib.tti_forward_opts(g.struct(), 4, w.dt, w.nt, 1, P(m), None, P(e), P(d), P(th),
                                   P(ph), 1, P(sx), P(sw), w.rec_xyz.shape[1], P(rx), P(rec),
