@@ -36,8 +36,11 @@ struct TfCfg {
     static constexpr int BX = 4 * TX, BY = TY;
     static constexpr int RA = 4;  // x halo in whole float4 cells (R <= 4)
     static_assert(R >= 1 && R <= 4, "the fused TTI kernel covers radii 1..4");
-    static constexpr int PX = BX + 4 * RA, PY = BY + 4 * R;   // p/r plane box
-    static constexpr int NXW = BX + 2 * RA, NYH = BY + 2 * R;  // cross bounding box
+    // p/r plane box (its rows carry 4 extra columns so that the x-strip
+    // cells, one per row and 8 rows per phase of a 128-bit shared access,
+    // fall on distinct banks) and the cross bounding box
+    static constexpr int PX = BX + 4 * RA + 4, PY = BY + 4 * R;
+    static constexpr int NXW = BX + 2 * RA, NYH = BY + 2 * R;
     static constexpr int GROUP = TX * TY, THREADS = 2 * GROUP, WARPS = THREADS / 32;
     static constexpr int INT = BX * BY;
     static constexpr int BOX = (PX * PY + 31) / 32 * 32;
