@@ -100,7 +100,8 @@ def roofline_of(family, st, peak, peak_kind, traffic=None):
     launch_ms = ms / max(n, 1)
     achieved = bpp * pts / (launch_ms * 1e-3) / 1e9 if n else 0.0
     return {"bound": "hbm", "kernel": family, "achieved": round(achieved, 1), "peak": peak,
-            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+            "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "frac_of_nominal_8000": round(achieved / 8000.0, 4), "traffic": traffic,
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
             if peak_kind == "measured" else "fallback 6.8 TB/s",
             "bytes_per_point": bpp, "launch_ms": round(launch_ms, 4), "launches": int(n)}
@@ -315,6 +316,7 @@ def run_ours(args):
         per_so[str(so)].update({
             "kernel": main, "kernel_gbs": round(alg / (kms * 1e-3) / 1e9, 1),
             "kernel_frac": round(alg / (kms * 1e-3) / 1e9 / peak, 4),
+            "kernel_frac_of_nominal_8000": round(alg / (kms * 1e-3) / 1e9 / 8000.0, 4),
             "kernel_gpts": round(pts_ * steps / (kms * 1e-3) / 1e9, 2),
             "bytes_per_point_step": round(alg / (pts_ * steps), 2)})
 
@@ -665,11 +667,33 @@ def cpu_baseline(w, so_list):
                                 damp=w.damp)
         t_total += time.perf_counter() - t0
         pts += float(w.npoints)
-    return {"value": round(pts / t_total / 1e9, 4), "unit": "GPts/s", "cores": cores,
-            "kind": "oracle",
-            "sample": f"1 time step at each so in {list(so_list)} of the {w.shape[0]}^3 workload "
-                      "(FP64 C oracle, OpenMP over all host cores, setup included)",
-            "seconds": round(t_total, 2)}
+    out = {"value": round(pts / t_total / 1e9, 4), "unit": "GPts/s", "cores": cores,
+           "kind": "oracle",
+           "sample": f"1 time step at each so in {list(so_list)} of the {w.shape[0]}^3 workload "
+                     "(FP64 C oracle, OpenMP over all host cores, setup included)",
+           "seconds": round(t_total, 2)}
+    # the same oracle on one core, on a 256^3 sample of the workload recipe
+    code = ("import json, time, oracle, workloads\n"
+            "w = workloads.acoustic_large(n=256, so=4)\n"
+            "g = oracle.make_grid(w.shape, w.spacing, w.origin)\n"
+            "t = 0.0\n"
+            f"for so in {list(so_list)}:\n"
+            "    t0 = time.perf_counter()\n"
+            "    oracle.acoustic_forward(g, so, w.dt, 2, w.m, w.src_xyz, w.src_wav[:, :2], "
+            "w.rec_xyz, damp=w.damp)\n"
+            "    t += time.perf_counter() - t0\n"
+            f"print(json.dumps({{'seconds': t, 'points': float(w.npoints) * {len(so_list)}}}))\n")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                           env={**os.environ, "OMP_NUM_THREADS": "1"}, timeout=300)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        out["single_thread"] = {"value": round(d["points"] / d["seconds"] / 1e9, 5),
+                                "unit": "GPts/s", "cores": 1, "seconds": round(d["seconds"], 2),
+                                "sample": f"1 time step at each so in {list(so_list)} of the "
+                                          "256^3 version of the workload"}
+    except Exception as exc:  # the single-core figure is informative only
+        out["single_thread"] = {"error": str(exc)[:200]}
+    return out
 
 
 def run_reference(args):
