@@ -356,8 +356,10 @@ int fd_num_time_tiling_configs(int so);
  * Launch configuration override of the two TTI passes (prefetch depths and
  * loop unroll; for tuning sweeps): index into the compiled table for the
  * given space order (0 .. fd_num_tti_configs(so) - 1), or -1 for the
- * built-in choice.  Applies to centred derivatives; the staggered reading
- * always uses the built-in choice.  Process-wide; FD_ERR_ARG if out of range.
+ * built-in choice.  Applies to centred derivatives of the two-pass scheme
+ * (the staggered reading always uses the built-in choice); for the fused
+ * scheme configuration 1 selects 64 x 16 tiles instead of 64 x 8 (other
+ * values: the built-in choice).  Process-wide; FD_ERR_ARG if out of range.
  */
 fd_status fd_set_tti_config(int so, int config);
 int fd_num_tti_configs(int so);

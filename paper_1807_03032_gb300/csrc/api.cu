@@ -769,7 +769,8 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
 
     TtiPlan tplan;
     if (fused)
-        FD_TRY(tti_fused_plan(R, stag ? 1 : 0, L, nshots, wave, bcoef, &tplan));
+        FD_TRY(tti_fused_plan(R, stag ? 1 : 0, L, nshots, wave, bcoef, &tplan,
+                              g_tti_config[R] < 0 ? 0 : g_tti_config[R]));
     else
         FD_TRY(tti_plan(R, L, nshots, wave, tmp, bcoef, &tplan, stag ? 1 : 0,
                         two_pass ? kTtiTwoPass : kTtiRecompute, g_tti_config[R]));

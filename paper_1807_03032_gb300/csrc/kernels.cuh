@@ -232,7 +232,7 @@ int tti_num_configs(int radius);
 // memory; radii 1, 2 and 4.
 bool tti_fused_supported(int radius);
 fd_status tti_fused_plan(int radius, int stag, const WaveLayout &L, int nshots, float *wave,
-                         const float *coef, TtiPlan *plan);
+                         const float *coef, TtiPlan *plan, int config = 0);
 fd_status tti_fused_launch(const TtiPlan &plan, const TtiArgs &a, cudaStream_t stream);
 fd_status tti_launch(const TtiPlan &plan, const TtiArgs &a, cudaStream_t stream,
                      cudaEvent_t *ev /* 3 events or null */);

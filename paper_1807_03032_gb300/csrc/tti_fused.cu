@@ -30,9 +30,9 @@ namespace fdsweep {
 namespace {
 using namespace tti;
 
-template <int R, int D>
+template <int R, int D, int TY_>
 struct TfCfg {
-    static constexpr int TX = 16, TY = 8;
+    static constexpr int TX = 16, TY = TY_;
     static constexpr int BX = 4 * TX, BY = TY;
     static constexpr int RA = 4;  // x halo in whole float4 cells (R <= 4)
     static_assert(R >= 1 && R <= 4, "the fused TTI kernel covers radii 1..4");
@@ -66,14 +66,14 @@ __device__ __forceinline__ void group_sync(int group, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + group), "r"(nthreads) : "memory");
 }
 
-template <int R, int D, int K1, int K2>
-__global__ void __launch_bounds__(256)
+template <int R, int D, int K1, int K2, int TY>
+__global__ void __launch_bounds__(32 * TY)
     tti_fused_kernel(const __grid_constant__ CUtensorMap map_box,
                      const __grid_constant__ CUtensorMap map_nbox,
                      const __grid_constant__ CUtensorMap map_wint,
                      const __grid_constant__ CUtensorMap map_cint, const TtiArgs a, int zchunk,
                      int nzc) {
-    using C = TfCfg<R, D>;
+    using C = TfCfg<R, D, TY>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *smem = reinterpret_cast<float *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
@@ -340,54 +340,56 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-template <int R, int STAG>
+template <int R, int STAG, int TY>
 const void *fused_fn() {
-    return (const void *)&tti_fused_kernel<R, 1, STAG ? 1 : 0, STAG ? -1 : 0>;
+    return (const void *)&tti_fused_kernel<R, 1, STAG ? 1 : 0, STAG ? -1 : 0, TY>;
 }
 
-bool fused_info(int radius, int stag, const void **fn, size_t *smem, int *px, int *py, int *nxw,
-                int *nyh) {
-#define FD_TF_CASE(RR)                                                                   \
-    case RR:                                                                             \
-        *fn = stag ? fused_fn<RR, 1>() : fused_fn<RR, 0>();                              \
-        *smem = TfCfg<RR, 1>::SMEM;                                                      \
-        *px = TfCfg<RR, 1>::PX;                                                          \
-        *py = TfCfg<RR, 1>::PY;                                                          \
-        *nxw = TfCfg<RR, 1>::NXW;                                                        \
-        *nyh = TfCfg<RR, 1>::NYH;                                                        \
-        return true;
+struct FusedInfo {
+    const void *fn;
+    size_t smem;
+    int px, py, nxw, nyh, by, threads;
+};
+
+template <int R, int TY>
+FusedInfo fused_info_t(int stag) {
+    using C = TfCfg<R, 1, TY>;
+    return FusedInfo{stag ? fused_fn<R, 1, TY>() : fused_fn<R, 0, TY>(), C::SMEM, C::PX, C::PY,
+                     C::NXW, C::NYH, C::BY, C::THREADS};
+}
+
+// Configuration 0: 64 x 8 tiles, two CTAs per SM; configuration 1: 64 x 16
+// tiles (fewer recomputed cross cells per tile point), one CTA per SM.
+bool fused_info(int radius, int stag, int config, FusedInfo *out) {
+    const bool tall = config == 1;
     switch (radius) {
-        FD_TF_CASE(1)
-        FD_TF_CASE(2)
-        FD_TF_CASE(4)
+        case 1: *out = tall ? fused_info_t<1, 16>(stag) : fused_info_t<1, 8>(stag); return true;
+        case 2: *out = tall ? fused_info_t<2, 16>(stag) : fused_info_t<2, 8>(stag); return true;
+        case 4: *out = fused_info_t<4, 8>(stag); return true;
         default: return false;
     }
-#undef FD_TF_CASE
 }
 
 }  // namespace
 
 bool tti_fused_supported(int radius) {
-    const void *fn;
-    size_t smem;
-    int px, py, nxw, nyh;
-    return fused_info(radius, 0, &fn, &smem, &px, &py, &nxw, &nyh);
+    FusedInfo in;
+    return fused_info(radius, 0, 0, &in);
 }
 
 fd_status tti_fused_plan(int radius, int stag, const WaveLayout &L, int nshots, float *wave,
-                         const float *coef, TtiPlan *plan) {
-    const void *fn;
-    size_t smem;
-    int px, py, nxw, nyh;
-    if (!fused_info(radius, stag, &fn, &smem, &px, &py, &nxw, &nyh))
+                         const float *coef, TtiPlan *plan, int config) {
+    FusedInfo in;
+    if (!fused_info(radius, stag, config, &in))
         return set_error(FD_ERR_ARG, "the fused TTI scheme covers space orders up to 8");
-    FD_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FD_CUDA_TRY(cudaFuncSetAttribute(in.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)in.smem));
     int dev = 0, nsm = 0, per_sm = 0;
     FD_CUDA_TRY(cudaGetDevice(&dev));
     FD_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    FD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem));
+    FD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, in.fn, in.threads, in.smem));
     if (per_sm < 1) return set_error(FD_ERR_CUDA, "fused TTI kernel does not fit on an SM");
-    const int bx = 64, by = 8;
+    const int bx = 64, by = in.by;
     const int ntx = (L.nx + bx - 1) / bx, nty = (L.ny + by - 1) / by;
     const int64_t cols = (int64_t)ntx * nty * nshots, slots = (int64_t)nsm * per_sm;
     int nzc = 1;
@@ -404,16 +406,17 @@ fd_status tti_fused_plan(int radius, int stag, const WaveLayout &L, int nshots, 
     plan->radius = radius;
     plan->stag = stag ? 1 : 0;
     plan->scheme = kTtiFused;
+    plan->config = config == 1 ? 1 : 0;
     plan->grid = dim3(ntx, nty, nshots * nzc);
-    plan->block = dim3(256, 1, 1);
-    plan->smem1 = smem;
+    plan->block = dim3(in.threads, 1, 1);
+    plan->smem1 = in.smem;
     plan->zchunk = zchunk;
     plan->nzc = nzc;
     const uint64_t sy = (uint64_t)L.nxp * 4, sz = (uint64_t)L.plane * 4, sw = (uint64_t)L.vol * 4;
     FD_TRY(make_tensor_map_4d(&plan->map_fbox, wave, L.nx, L.ny, L.nz, 4ull * nshots, sy, sz, sw,
-                              px, py, 1, 1));
-    FD_TRY(make_tensor_map_4d(&plan->map_fnbox, coef, L.nx, L.ny, L.nz, 6, sy, sz, sw, nxw, nyh,
-                              1, 1));
+                              in.px, in.py, 1, 1));
+    FD_TRY(make_tensor_map_4d(&plan->map_fnbox, coef, L.nx, L.ny, L.nz, 6, sy, sz, sw, in.nxw,
+                              in.nyh, 1, 1));
     FD_TRY(make_tensor_map_4d(&plan->map_wint, wave, L.nx, L.ny, L.nz, 4ull * nshots, sy, sz, sw,
                               bx, by, 1, 1));
     return make_tensor_map_4d(&plan->map_cint, coef, L.nx, L.ny, L.nz, 6, sy, sz, sw, bx, by, 1,
@@ -421,15 +424,13 @@ fd_status tti_fused_plan(int radius, int stag, const WaveLayout &L, int nshots, 
 }
 
 fd_status tti_fused_launch(const TtiPlan &plan, const TtiArgs &a, cudaStream_t stream) {
-    const void *fn;
-    size_t smem;
-    int px, py, nxw, nyh;
-    if (!fused_info(plan.radius, plan.stag, &fn, &smem, &px, &py, &nxw, &nyh))
+    FusedInfo in;
+    if (!fused_info(plan.radius, plan.stag, plan.config, &in))
         return set_error(FD_ERR_SO, "bad fused TTI plan");
     int zchunk = plan.zchunk, nzc = plan.nzc;
     void *params[] = {(void *)&plan.map_fbox, (void *)&plan.map_fnbox, (void *)&plan.map_wint,
                       (void *)&plan.map_cint, (void *)&a, (void *)&zchunk, (void *)&nzc};
-    FD_CUDA_TRY(cudaLaunchKernel(fn, plan.grid, plan.block, params, plan.smem1, stream));
+    FD_CUDA_TRY(cudaLaunchKernel(in.fn, plan.grid, plan.block, params, plan.smem1, stream));
     note_launch(stream);
     return FD_OK;
 }
