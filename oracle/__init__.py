@@ -95,12 +95,17 @@ def _load():
             lib.ora_tti_forward_opts.argtypes = [G, I, I, I, I, D, I, I, P, P, P, P, P, P,
                                                  I, P, P, I, P, P, P, P, P, P]
             lib.ora_acoustic_adjoint.argtypes = [G, I, I, D, I, I, P, P, I, P, P, I, P, P]
+            lib.ora_round_binary16.argtypes = [D]
+            lib.ora_round_binary16.restype = D
+            lib.ora_acoustic_forward_storage.argtypes = [G, I, I, D, I, I, P, P, I, P, P, I, P,
+                                                         P, P, P, I]
             lib.ora_acoustic_gradient.argtypes = [G, I, D, I, I, P, P, I, P, P, I, P, P, P]
             for name in ("ora_acoustic_adjoint", "ora_acoustic_gradient",
                          "ora_laplacian", "ora_first_derivative", "ora_acoustic_step",
                          "ora_interpolate", "ora_inject", "ora_acoustic_forward",
                          "ora_tti_operators", "ora_tti_forward", "ora_first_derivative_kind",
-                         "ora_tti_operators_kind", "ora_tti_forward_opts"):
+                         "ora_tti_operators_kind", "ora_tti_forward_opts",
+                         "ora_acoustic_forward_storage"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -224,6 +229,43 @@ def acoustic_forward(grid: Grid, so: int, dt: float, nt: int, m, src_xyz, src_wa
                                       _ptr(src_wav), nrec, _ptr(rec_xyz), _ptr(rec),
                                       _ptr(u_init), _ptr(ufin))
     _check(st, "acoustic_forward")
+    return rec, ufin
+
+
+_STORAGE = {"exact": 0, "f16": 1}
+
+
+def round_binary16(x):
+    """Nearest IEEE binary16 value of each element (ties to even), FP64 out."""
+    x = np.asarray(x, dtype=np.float64)
+    f = _load().ora_round_binary16
+    return np.vectorize(lambda v: f(float(v)), otypes=[np.float64])(x) if x.size else x.copy()
+
+
+def acoustic_forward_storage(grid: Grid, so: int, dt: float, nt: int, m, src_xyz, src_wav,
+                             rec_xyz, damp=None, u_init=None, storage: str = "f16",
+                             periodic: bool = False):
+    """Acoustic forward model with reduced-precision storage.
+
+    storage "f16": the wavefield levels and the coefficient b = dt^2/(m +
+    damp dt/2) are stored in IEEE binary16 (values the device computes in FP32
+    are rounded to FP32, then to binary16); "exact": no rounding (the same
+    model as acoustic_forward, update written in the b form).  Shapes and
+    return values as acoustic_forward.
+    """
+    m = _f32(m)
+    damp = _f32(damp)
+    src_xyz, src_wav, rec_xyz = _f32(src_xyz), _f32(src_wav), _f32(rec_xyz)
+    u_init = _f32(u_init)
+    nshots, nsrc = src_xyz.shape[0], src_xyz.shape[1]
+    nrec = rec_xyz.shape[1]
+    rec = np.zeros((nshots, nt, nrec))
+    ufin = np.zeros((nshots, 2) + m.shape)
+    st = _load().ora_acoustic_forward_storage(
+        ctypes.byref(grid), so, int(periodic), float(dt), int(nt), nshots, _ptr(m), _ptr(damp),
+        nsrc, _ptr(src_xyz), _ptr(src_wav), nrec, _ptr(rec_xyz), _ptr(rec), _ptr(u_init),
+        _ptr(ufin), _STORAGE[storage])
+    _check(st, "acoustic_forward_storage")
     return rec, ufin
 
 

@@ -386,6 +386,147 @@ done:
 }
 
 /*
+ * ---- Reduced-precision storage ------------------------------------------
+ *
+ * The paper lists mixed-precision arithmetic and on-the-fly data compression
+ * among its further performance work (section "Future work").  Reading used
+ * here: the bulk fields are STORED in IEEE binary16 and all arithmetic stays
+ * in FP32 on the device; the oracle models the storage exactly and keeps its
+ * own arithmetic in FP64.  What is stored:
+ *   - the wavefield levels u^n, u^{n-1} (every value written is rounded);
+ *   - the coefficient b = dt^2 / (m + damp dt/2) that multiplies the
+ *     Laplacian and the injected source.
+ * A value that the device computes in FP32 and then stores is rounded to
+ * FP32 first and to binary16 second (the decision taken in the device's
+ * precision); the sum of two binary16 values (source injection into a stored
+ * field) is rounded once.
+ */
+
+/* Nearest IEEE binary16 value of x, ties to even, as a double.  From the
+ * format's definition: 11 significant bits for normal numbers (unbiased
+ * exponents -14..15); below 2^-14 the spacing is fixed at 2^-24 (subnormal
+ * numbers); magnitudes from 65520 (the midpoint between the largest finite
+ * value 65504 and 2^16) up round to infinity.  The sign of zero and NaN are
+ * kept. */
+double ora_round_binary16(double x) {
+    if (x != x) return x;
+    const double a = fabs(x);
+    if (a == 0.0) return x;
+    if (a >= 65520.0) return copysign(INFINITY, x);
+    int e2;
+    frexp(a, &e2); /* a in [2^(e2-1), 2^e2) */
+    int ex = e2 - 1;
+    if (ex < -14) ex = -14;
+    const double q = ldexp(1.0, ex - 10); /* spacing of binary16 values near a */
+    return copysign(nearbyint(a / q) * q, x); /* a / q exact; default mode: ties to even */
+}
+
+/* A value computed on the device in FP32 and stored in binary16. */
+static double store16(double x) { return ora_round_binary16((double)(float)x); }
+
+/*
+ * Acoustic forward model with the storage of `storage`:
+ *   0  no rounding: the same model as ora_acoustic_forward, with the update
+ *      written in the b form below (equal to it up to FP64 rounding);
+ *   1  binary16 storage of u and b as described above.
+ * The update in b form (b = dt^2/(m + eta), eta = damp dt/2; algebraically
+ * the damped leapfrog update of ora_acoustic_forward):
+ *   u+ = u + (1 - b damp/dt)(u - u-) + b lap(u).
+ * Per step n: u^{n+1} = S(update); then for every source p and corner c in
+ * order, u^{n+1}[node] = S16(u^{n+1}[node] + S(w_c b[node] q_p[n])), where S
+ * is store16 (storage 1) or the identity, and S16 the single binary16
+ * rounding of the exact sum; rec[n] = interp(u^n).  Shapes as in
+ * ora_acoustic_forward; u_init is rounded on entry; u_final holds the stored
+ * values.
+ */
+int ora_acoustic_forward_storage(const ora_grid *g, int so, int periodic, double dt, int nt,
+                                 int nshots, const float *m32, const float *damp32, int nsrc,
+                                 const float *src_xyz, const float *src_wav, int nrec,
+                                 const float *rec_xyz, double *rec_out, const float *u_init,
+                                 double *u_final, int storage) {
+    if (radius_of(so) < 0 || nt < 1 || nshots < 1 || nsrc < 0 || nrec < 0 || storage < 0 ||
+        storage > 1)
+        return ORA_ERR_ARG;
+    const size_t N = npts(g);
+    for (int s = 0; s < nshots; ++s) {
+        if (check_sparse(g, nsrc, src_xyz + (size_t)s * nsrc * 3)) return ORA_ERR_COORD;
+        if (check_sparse(g, nrec, rec_xyz + (size_t)s * nrec * 3)) return ORA_ERR_COORD;
+    }
+    double *m = widen(m32, N);
+    double *damp = damp32 ? widen(damp32, (size_t)g->nx + g->ny + g->nz) : NULL;
+    double *b = (double *)malloc(N * sizeof(double));
+    double *lap = (double *)malloc(N * sizeof(double));
+    double *u = (double *)malloc(N * sizeof(double));
+    double *um = (double *)malloc(N * sizeof(double));
+    double *un = (double *)malloc(N * sizeof(double));
+    int st = ORA_OK;
+    if (!m || (damp32 && !damp) || !b || !lap || !u || !um || !un) {
+        st = ORA_ERR_OOM;
+        goto done;
+    }
+    injection_scale(g, dt, m, damp, b); /* b = dt^2 / (m + damp dt/2) */
+    if (storage == 1)
+        for (size_t p = 0; p < N; ++p) b[p] = store16(b[p]);
+    for (int s = 0; s < nshots; ++s) {
+        const float *sxyz = src_xyz + (size_t)s * nsrc * 3;
+        const float *rxyz = rec_xyz + (size_t)s * nrec * 3;
+        double *rec = rec_out ? rec_out + (size_t)s * nt * nrec : NULL;
+        for (size_t p = 0; p < N; ++p) {
+            u[p] = u_init ? (double)u_init[((size_t)s * 2 + 0) * N + p] : 0.0;
+            um[p] = u_init ? (double)u_init[((size_t)s * 2 + 1) * N + p] : 0.0;
+            if (storage == 1) {
+                u[p] = store16(u[p]);
+                um[p] = store16(um[p]);
+            }
+        }
+        for (int n = 0; n + 1 < nt; ++n) {
+            st = ora_laplacian(g, so, periodic, u, lap);
+            if (st) goto done;
+            for (int k = 0; k < g->nz; ++k)
+                for (int j = 0; j < g->ny; ++j)
+                    for (int i = 0; i < g->nx; ++i) {
+                        const size_t p = lin(g, i, j, k);
+                        const double zeta = b[p] * damp_at(g, damp, i, j, k) / dt;
+                        const double v = u[p] + (1.0 - zeta) * (u[p] - um[p]) + b[p] * lap[p];
+                        un[p] = storage == 1 ? store16(v) : v;
+                    }
+            for (int p = 0; p < nsrc; ++p) {
+                size_t idx[8];
+                double w[8];
+                sparse_point(g, sxyz + 3 * (size_t)p, idx, w);
+                const double q = (double)src_wav[((size_t)s * nt + n) * nsrc + p];
+                for (int c = 0; c < 8; ++c) {
+                    const double add = w[c] * b[idx[c]] * q;
+                    if (storage == 1)
+                        un[idx[c]] = ora_round_binary16(un[idx[c]] + store16(add));
+                    else
+                        un[idx[c]] += add;
+                }
+            }
+            if (rec) ora_interpolate(g, nrec, rxyz, u, rec + (size_t)n * nrec);
+            double *t = um;
+            um = u;
+            u = un;
+            un = t;
+        }
+        if (rec) ora_interpolate(g, nrec, rxyz, u, rec + (size_t)(nt - 1) * nrec);
+        if (u_final) {
+            memcpy(u_final + ((size_t)s * 2 + 0) * N, u, N * sizeof(double));
+            memcpy(u_final + ((size_t)s * 2 + 1) * N, um, N * sizeof(double));
+        }
+    }
+done:
+    free(m);
+    free(damp);
+    free(b);
+    free(lap);
+    free(u);
+    free(um);
+    free(un);
+    return st;
+}
+
+/*
  * TTI operators for one field q: Hz q = sum_i D_i(n_i (n . grad q)) and
  * L q = sum_i D_i D_i q, with n = (sin t cos f, sin t sin f, cos t) per point.
  * deriv = 0: D is the central first derivative of order so (inner and outer);
