@@ -371,6 +371,12 @@ def run_ours(args):
                "unit": "GPts/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "steps": ksteps, "host_memory": "pinned"}
 
+    # ---------------------------------------------------------------- binary16 storage
+    storage_f16 = None
+    if not args.no_f16:
+        storage_f16 = run_storage_f16(args, fd, _native, g, w, m, damp, sxyz, swav, rxyz,
+                                      stream, peak, per_so)
+
     # ---------------------------------------------------------------- TTI
     tti = None
     if not args.no_tti:
@@ -414,6 +420,7 @@ def run_ours(args):
             "roofline": roofline,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "storage_f16": storage_f16,
             "tti": tti,
             "fwi_gradient": fwi,
             "serving": serving,
@@ -424,6 +431,52 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_storage_f16(args, fd, _native, g, w, m, damp, sxyz, swav, rxyz, stream, peak, per_so):
+    """The same forward runs with the wavefields and b stored in binary16
+    (FP32 arithmetic): whole-call and kernel rates, the kernel's HBM
+    fraction at 8 algorithmic bytes per point, and the distance of its
+    traces from the FP32 run's."""
+    import torch
+    nrec = rxyz.shape[1]
+    rec32 = torch.empty((1, w.nt, nrec), dtype=torch.float32, device=m.device)
+    rec16 = torch.empty_like(rec32)
+    pts = float(w.npoints) * (w.nt - 1)
+    out = {"what": "acoustic_forward_opts with FD_STORAGE_F16: u^n, u^{n-1} and b held in "
+                   "IEEE binary16, FP32 arithmetic; one forward per so of the same workload",
+           "bytes_per_point": 8, "per_so": {}}
+    for so in args.so:
+        fd.acoustic_forward(g, so, w.dt, w.nt, m, sxyz, swav, rxyz, damp=damp, rec_out=rec32,
+                            return_final=False)
+        fd.acoustic_forward(g, so, w.dt, 20, m, sxyz, swav[:, :20].contiguous(), rxyz,
+                            damp=damp, return_final=False, storage="f16")
+        _native.stats_reset()
+        _native.stats_enable(True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fd.acoustic_forward(g, so, w.dt, w.nt, m, sxyz, swav, rxyz, damp=damp, rec_out=rec16,
+                            return_final=False, storage="f16")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        kms, nl, npts = _native.stats_get("acoustic_step_h")
+        _native.stats_enable(False)
+        per = kms / max(nl, 1)
+        gbs = 8.0 * npts / (per * 1e-3) / 1e9
+        rel = float(torch.linalg.vector_norm((rec16 - rec32).double()) /
+                    torch.linalg.vector_norm(rec32.double()))
+        kg = npts / (per * 1e-3) / 1e9
+        row = {"gpts": round(pts / (ms * 1e-3) / 1e9, 2), "kernel_gpts": round(kg, 2),
+               "kernel_gbs": round(gbs, 1), "kernel_frac": round(gbs / peak, 4),
+               "traces_rel_l2_vs_f32": float(f"{rel:.3e}")}
+        k32 = per_so.get(str(so), {}).get("kernel_gpts")
+        if k32:
+            row["kernel_speedup_vs_f32"] = round(kg / k32, 3)
+        out["per_so"][str(so)] = row
+    return out
 
 
 def run_tti(args, fd, _native, dev, stream, peak):
@@ -746,6 +799,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tti", action="store_true")
     ap.add_argument("--no-tti-ablation", action="store_true")
+    ap.add_argument("--no-f16", action="store_true",
+                    help="skip the binary16-storage runs")
     ap.add_argument("--time-tiling", type=int, default=-1,
                     help="fd_set_time_tiling mode for every space order (-1 automatic, "
                          "0 off, 1 + k two-step kernel configuration k)")

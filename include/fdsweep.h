@@ -101,6 +101,45 @@ fd_status acoustic_forward(const fd_grid *grid, int so, double dt, int nt, int n
                            const float *u_init, float *u_final, void *stream);
 
 /*
+ * acoustic_forward_opts -- acoustic_forward with a choice of storage
+ * precision.  The paper names mixed-precision arithmetic and on-the-fly data
+ * compression as further performance work (section "Future work"); the step
+ * is memory bound, so halving the stored bytes per point is the lever.
+ *
+ *   opts->storage  FD_STORAGE_F32: FP32 storage, identical to acoustic_forward.
+ *                  FD_STORAGE_F16: the wavefield levels and the coefficient
+ *                  b = dt^2/(m + damp dt/2) are held in IEEE binary16 on the
+ *                  device (8 instead of 16 bytes per point and step); every
+ *                  value is decoded exactly to FP32, the update and the
+ *                  sparse operations compute in FP32, and each stored result
+ *                  is rounded to the nearest binary16 (ties to even; a source
+ *                  contribution is rounded to binary16 and added with one
+ *                  more rounding).  u_init is rounded on entry; u_final and
+ *                  the traces are the FP32 values of the stored binary16
+ *                  fields.  The stored values carry a relative rounding error
+ *                  of up to 2^-11 per step, which accumulates: expect traces
+ *                  within about 1e-3 and late wavefields within about 1e-2 of
+ *                  the FP32 result after a few hundred steps, and no value
+ *                  above 65504 in magnitude (beyond it the run reports
+ *                  FD_ERR_DIVERGED).  Radii with a binary16 kernel: so = 2..16
+ *                  (FD_ERR_UNIMPL otherwise); time tiling is not combined
+ *                  with it.
+ *   opts           NULL selects FD_STORAGE_F32.  Out-of-range values return
+ *                  FD_ERR_ARG.
+ * Other arguments, ownership and errors as for acoustic_forward.
+ */
+enum { FD_STORAGE_F32 = 0, FD_STORAGE_F16 = 1 };
+typedef struct {
+    int32_t storage;
+} fd_acoustic_options;
+
+fd_status acoustic_forward_opts(const fd_grid *grid, int so, double dt, int nt, int nshots,
+                                const float *m, const float *damp, int nsrc,
+                                const float *src_xyz, const float *src_wav, int nrec,
+                                const float *rec_xyz, float *rec_out, const float *u_init,
+                                float *u_final, const fd_acoustic_options *opts, void *stream);
+
+/*
  * tti_forward -- tilted transverse isotropy (TTI) forward model.
  *
  * Two coupled acoustic equations whose Laplacians are built from rotated
@@ -320,6 +359,7 @@ const char *fd_version(void);
  * times are accumulated per kernel family when the call completes.
  * Families: "acoustic_step", "acoustic_step2" (two time steps per launch, see
  * fd_set_time_tiling; points_per_launch counts the points of one step),
+ * "acoustic_step_h" (binary16 storage, acoustic_forward_opts),
  * "tti_pass1", "tti_pass2", "tti_recompute", "tti_fused" (the one-kernel TTI
  * schemes of tti_forward_opts), "sparse".
  * fd_stats_get returns FD_ERR_ARG for an unknown family.
@@ -371,6 +411,11 @@ int fd_num_tti_configs(int so);
  */
 fd_status fd_set_acoustic_config(int so, int config);
 int fd_num_acoustic_configs(int so);
+
+/* The same for the binary16-storage kernel (acoustic_forward_opts with
+ * FD_STORAGE_F16); 0 configurations for a space order without one. */
+fd_status fd_set_acoustic_f16_config(int so, int config);
+int fd_num_acoustic_f16_configs(int so);
 
 #ifdef __cplusplus
 }

@@ -232,7 +232,7 @@ def acoustic_forward(grid: Grid, so: int, dt: float, nt: int, m, src_xyz, src_wa
     return rec, ufin
 
 
-_STORAGE = {"exact": 0, "f16": 1}
+_STORAGE = {"exact": 0, "f16": 1, "f16_coef": 2}
 
 
 def round_binary16(x):
@@ -249,9 +249,11 @@ def acoustic_forward_storage(grid: Grid, so: int, dt: float, nt: int, m, src_xyz
 
     storage "f16": the wavefield levels and the coefficient b = dt^2/(m +
     damp dt/2) are stored in IEEE binary16 (values the device computes in FP32
-    are rounded to FP32, then to binary16); "exact": no rounding (the same
-    model as acoustic_forward, update written in the b form).  Shapes and
-    return values as acoustic_forward.
+    are rounded to FP32, then to binary16); "f16_coef": only b is stored in
+    binary16, the wavefields stay exact (one step of it, rounded, is one step
+    of "f16"); "exact": no rounding (the same model as acoustic_forward,
+    update written in the b form).  Shapes and return values as
+    acoustic_forward.
     """
     m = _f32(m)
     damp = _f32(damp)

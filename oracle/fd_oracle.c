@@ -428,7 +428,9 @@ static double store16(double x) { return ora_round_binary16((double)(float)x); }
  * Acoustic forward model with the storage of `storage`:
  *   0  no rounding: the same model as ora_acoustic_forward, with the update
  *      written in the b form below (equal to it up to FP64 rounding);
- *   1  binary16 storage of u and b as described above.
+ *   1  binary16 storage of u and b as described above;
+ *   2  binary16 storage of b only (u kept exact): one step of it, stored,
+ *      is one step of storage 1.
  * The update in b form (b = dt^2/(m + eta), eta = damp dt/2; algebraically
  * the damped leapfrog update of ora_acoustic_forward):
  *   u+ = u + (1 - b damp/dt)(u - u-) + b lap(u).
@@ -445,7 +447,7 @@ int ora_acoustic_forward_storage(const ora_grid *g, int so, int periodic, double
                                  const float *rec_xyz, double *rec_out, const float *u_init,
                                  double *u_final, int storage) {
     if (radius_of(so) < 0 || nt < 1 || nshots < 1 || nsrc < 0 || nrec < 0 || storage < 0 ||
-        storage > 1)
+        storage > 2)
         return ORA_ERR_ARG;
     const size_t N = npts(g);
     for (int s = 0; s < nshots; ++s) {
@@ -465,7 +467,7 @@ int ora_acoustic_forward_storage(const ora_grid *g, int so, int periodic, double
         goto done;
     }
     injection_scale(g, dt, m, damp, b); /* b = dt^2 / (m + damp dt/2) */
-    if (storage == 1)
+    if (storage >= 1)
         for (size_t p = 0; p < N; ++p) b[p] = store16(b[p]);
     for (int s = 0; s < nshots; ++s) {
         const float *sxyz = src_xyz + (size_t)s * nsrc * 3;

@@ -88,12 +88,14 @@ def _as_grid(grid):
 
 
 def acoustic_forward(grid, so, dt, nt, m, src_xyz, src_wav, rec_xyz, damp=None, u_init=None,
-                     rec_out=None, u_final=None, return_final=True, stream=None):
+                     rec_out=None, u_final=None, return_final=True, stream=None, storage="f32"):
     """Isotropic acoustic forward model (C ABI ``acoustic_forward``).
 
     m [nz][ny][nx]; damp [nx+ny+nz] per-axis profiles or None;
     src_xyz [nshots][nsrc][3]; src_wav [nshots][nt][nsrc]; rec_xyz [nshots][nrec][3];
     u_init [nshots][2][nz][ny][nx] (u^0, u^-1) or None.
+    storage: "f32" or "f16" (wavefields and b held in IEEE binary16 on the
+    device, FP32 arithmetic; C ABI ``acoustic_forward_opts``).
     Returns (rec [nshots][nt][nrec], u_final [nshots][2][nz][ny][nx] or None).
     Outputs are allocated like ``m`` (same device / host) unless given.
     """
@@ -109,11 +111,16 @@ def acoustic_forward(grid, so, dt, nt, m, src_xyz, src_wav, rec_xyz, damp=None, 
     if u_final is None and return_final:
         u_final = _empty_like_kind(m, (nshots, 2) + tuple(g.shape))
     lib = _native.load()
-    st = lib.acoustic_forward(
-        g.struct(), int(so), float(dt), int(nt), nshots, _ptr(m, "m"), _ptr(damp, "damp"), nsrc,
-        _ptr(src_xyz, "src_xyz"), _ptr(src_wav, "src_wav"), nrec, _ptr(rec_xyz, "rec_xyz"),
-        _ptr(rec_out, "rec_out"), _ptr(u_init, "u_init"), _ptr(u_final, "u_final"),
-        _stream_for(m, rec_out, stream=stream))
+    args = (g.struct(), int(so), float(dt), int(nt), nshots, _ptr(m, "m"), _ptr(damp, "damp"),
+            nsrc, _ptr(src_xyz, "src_xyz"), _ptr(src_wav, "src_wav"), nrec,
+            _ptr(rec_xyz, "rec_xyz"), _ptr(rec_out, "rec_out"), _ptr(u_init, "u_init"),
+            _ptr(u_final, "u_final"))
+    stream_ptr = _stream_for(m, rec_out, stream=stream)
+    if storage == "f32":
+        st = lib.acoustic_forward(*args, stream_ptr)
+    else:
+        opts = _native.FdAcousticOptions(_native.STORAGE[storage])
+        st = lib.acoustic_forward_opts(*args, ctypes.byref(opts), stream_ptr)
     _native.check(st)
     return rec_out, u_final
 

@@ -28,7 +28,8 @@ EXPORTED = ("acoustic_forward", "tti_forward", "tti_forward_opts", "fd_last_erro
             "acoustic_adjoint", "acoustic_gradient", "fd_engine_footprint", "fd_engine_create",
             "fd_engine_add_shot", "fd_engine_step", "fd_engine_shot_status", "fd_engine_release",
             "fd_engine_stream", "fd_engine_sync", "fd_engine_destroy", "fd_set_time_tiling",
-            "fd_num_time_tiling_configs", "fd_set_tti_config", "fd_num_tti_configs")
+            "fd_num_time_tiling_configs", "fd_set_tti_config", "fd_num_tti_configs",
+            "acoustic_forward_opts", "fd_set_acoustic_f16_config", "fd_num_acoustic_f16_configs")
 
 
 class FdGrid(ctypes.Structure):
@@ -46,6 +47,13 @@ class FdTtiOptions(ctypes.Structure):
                 ("scheme", ctypes.c_int32)]
 
 
+class FdAcousticOptions(ctypes.Structure):
+    """Mirror of fd_acoustic_options."""
+
+    _fields_ = [("storage", ctypes.c_int32)]
+
+
+STORAGE = {"f32": 0, "f16": 1}
 TTI_DERIV = {"centred": 0, "staggered": 1}
 TTI_RECEIVER = {"p": 0, "mean": 1}
 TTI_SCHEME = {"auto": -1, "two_pass": 0, "recompute": 1, "fused": 2}
@@ -77,6 +85,13 @@ def load(path: str = LIB_PATH):
         G = ctypes.POINTER(FdGrid)
         lib.acoustic_forward.argtypes = [G, I, D, I, I, P, P, I, P, P, I, P, P, P, P, P]
         lib.acoustic_forward.restype = I
+        lib.acoustic_forward_opts.argtypes = [G, I, D, I, I, P, P, I, P, P, I, P, P, P, P,
+                                              ctypes.POINTER(FdAcousticOptions), P]
+        lib.acoustic_forward_opts.restype = I
+        lib.fd_set_acoustic_f16_config.argtypes = [I, I]
+        lib.fd_set_acoustic_f16_config.restype = I
+        lib.fd_num_acoustic_f16_configs.argtypes = [I]
+        lib.fd_num_acoustic_f16_configs.restype = I
         lib.acoustic_forward_noalloc.argtypes = [G, I, D, I, I, P, P, I, P, P, I, P, P, P, P, P]
         lib.acoustic_forward_noalloc.restype = I
         lib.acoustic_adjoint.argtypes = [G, I, D, I, I, P, P, I, P, P, I, P, P, P]
@@ -127,7 +142,8 @@ def load(path: str = LIB_PATH):
         for name in ("fd_engine_footprint", "fd_engine_create", "fd_engine_add_shot",
                      "fd_engine_step", "fd_engine_shot_status", "fd_engine_release",
                      "fd_engine_stream", "fd_engine_sync", "fd_engine_destroy", "fd_set_time_tiling",
-            "fd_num_time_tiling_configs", "fd_set_tti_config", "fd_num_tti_configs"):
+            "fd_num_time_tiling_configs", "fd_set_tti_config", "fd_num_tti_configs",
+            "acoustic_forward_opts", "fd_set_acoustic_f16_config", "fd_num_acoustic_f16_configs"):
             getattr(lib, name).restype = I
         lib.fd_launch_count.argtypes = []
         lib.fd_launch_count.restype = ctypes.c_int64
@@ -196,3 +212,11 @@ def set_acoustic_config(so: int, config: int):
 
 def num_acoustic_configs(so: int) -> int:
     return int(load().fd_num_acoustic_configs(int(so)))
+
+
+def set_acoustic_f16_config(so: int, config: int):
+    check(load().fd_set_acoustic_f16_config(int(so), int(config)))
+
+
+def num_acoustic_f16_configs(so: int) -> int:
+    return int(load().fd_num_acoustic_f16_configs(int(so)))

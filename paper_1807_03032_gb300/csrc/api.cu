@@ -657,6 +657,216 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     return flags_to_status(hs.flags, "acoustic_forward");
 }
 
+// ====================================================================== binary16 storage
+
+namespace {
+int g_acoustic_h_config[kMaxRadius + 1] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
+}  // namespace
+
+// acoustic_forward with the wavefield levels and b stored in IEEE binary16
+// (FP32 arithmetic).  Same schedule as the FP32 path without time tiling:
+// per step the stencil kernel, the injection of src[n] into u^{n+1}, and the
+// receivers of u^n on a side stream.
+static fd_status acoustic_forward_h_impl(const fd_grid *grid, int so, double dt, int nt,
+                                         int nshots, const float *m, const float *damp,
+                                         int nsrc, const float *src_xyz, const float *src_wav,
+                                         int nrec, const float *rec_xyz, float *rec_out,
+                                         const float *u_init, float *u_final,
+                                         cudaStream_t caller) {
+    FD_TRY(validate_common(grid, so, dt, nt, nshots, m, nsrc, src_xyz, src_wav, nrec, rec_xyz,
+                           rec_out));
+    const int R = so / 2;
+    if (acoustic_h_num_configs(R) == 0)
+        return set_error(FD_ERR_UNIMPL, "binary16 storage: no kernel for so = %d", so);
+    GridDerived gd = derive(grid, so);
+    const WaveLayout &L = gd.L;  // FP32 layout of the setup
+    WaveLayout LH = L;           // binary16 layout: 16-byte rows
+    LH.nxp = (L.nx + 7) / 8 * 8;
+    LH.plane = (int64_t)LH.nxp * L.ny;
+    LH.vol = LH.plane * L.nz;
+    const size_t dense = (size_t)L.nx * L.ny * L.nz;
+    const int64_t rows = (int64_t)L.ny * L.nz;
+    const int ndamp = L.nx + L.ny + L.nz;
+
+    CallStream cs;
+    FD_TRY(cs.begin(caller));
+    cudaStream_t s = cs.get();
+
+    Workspace ws;
+    half_bits *wave, *bh;
+    float *b32, *dps;
+    SparsePoint *src_tab, *rec_tab;
+    MediumStats *dstats;
+    int *counter;
+    ws.add(&wave, (size_t)2 * nshots * LH.vol);
+    ws.add(&bh, LH.vol);
+    ws.add(&b32, L.vol);
+    ws.add(&dps, ndamp);
+    ws.add(&src_tab, (size_t)nshots * nsrc);
+    ws.add(&rec_tab, (size_t)nshots * nrec);
+    ws.add(&dstats, 1);
+    ws.add(&counter, 1);
+    Staged sm, sdamp, ssxyz, swav, srxyz, sinit;
+    StagedOut srec, sfinal;
+    sm.plan(ws, m, dense);
+    sdamp.plan(ws, damp, damp ? ndamp : 0);
+    ssxyz.plan(ws, src_xyz, (size_t)nshots * nsrc * 3);
+    swav.plan(ws, src_wav, (size_t)nshots * nt * nsrc);
+    srxyz.plan(ws, rec_xyz, (size_t)nshots * nrec * 3);
+    sinit.plan(ws, u_init, u_init ? (size_t)nshots * 2 * dense : 0);
+    srec.plan(ws, rec_out, (size_t)nshots * nt * nrec);
+    sfinal.plan(ws, u_final, u_final ? (size_t)nshots * 2 * dense : 0);
+    FD_TRY(ws.allocate(s));
+    TraceStreamer traces;
+    FD_TRY(traces.begin(&srec, nshots, nt, nrec));
+    for (Staged *st : {&sm, &sdamp, &ssxyz, &swav, &srxyz, &sinit}) FD_TRY(st->place(s));
+    FD_STAGE(s, "acoustic f16: inputs staged");
+
+    // ---- K0: coefficients (FP64 -> FP32 as in the FP32 path, then binary16)
+    FD_CUDA_TRY(cudaMemsetAsync(b32, 0, (size_t)L.vol * 4, s));
+    FD_CUDA_TRY(cudaMemsetAsync(bh, 0, (size_t)LH.vol * 2, s));
+    FD_TRY(init_medium_stats(dstats, s));
+    FD_TRY(setup_acoustic_coeffs(sm.dev, sdamp.dev, dt, L, b32, dps, dstats, s));
+    FD_TRY(narrow_rows(b32, L.nxp, bh, LH.nxp, L.nx, rows, s));
+    for (int sh = 0; sh < nshots; ++sh) {
+        FD_TRY(setup_sparse_table(ssxyz.dev ? ssxyz.dev + (size_t)sh * nsrc * 3 : nullptr, nsrc,
+                                  *grid, LH, src_tab + (size_t)sh * nsrc, &dstats->flags, s));
+        FD_TRY(setup_sparse_table(srxyz.dev ? srxyz.dev + (size_t)sh * nrec * 3 : nullptr, nrec,
+                                  *grid, LH, rec_tab + (size_t)sh * nrec, &dstats->flags, s));
+    }
+    FD_TRY(finish_medium_stats(dstats, s));
+    MediumStats hs;
+    FD_TRY(read_stats(dstats, &hs, s));
+    FD_TRY(flags_to_status(hs.flags, "acoustic_forward_opts"));
+    {
+        const double vmax = 1.0 / sqrt((double)hs.m_min);
+        const double sig = second_symbol_max(R, gd.w);
+        const double lam = sig * (1.0 / (grid->hx * grid->hx) + 1.0 / (grid->hy * grid->hy) +
+                                  1.0 / (grid->hz * grid->hz));
+        const double dt_max = 2.0 / (vmax * sqrt(lam));
+        if (dt > dt_max * (1.0 + 1e-12))
+            return set_error(FD_ERR_CFL,
+                             "dt = %.6g ms exceeds the leapfrog stability bound %.6g ms "
+                             "(v_max = %.6g km/s, so = %d)",
+                             dt, dt_max, vmax, so);
+    }
+
+    // ---- initial state, rounded to binary16
+    FD_CUDA_TRY(cudaMemsetAsync(wave, 0, (size_t)2 * nshots * LH.vol * 2, s));
+    if (u_init)
+        for (int f = 0; f < 2 * nshots; ++f)
+            FD_TRY(narrow_rows(sinit.dev + (size_t)f * dense, L.nx, wave + (int64_t)f * LH.vol,
+                               LH.nxp, L.nx, rows, s));
+
+    AcousticPlan plan;
+    FD_TRY(acoustic_h_plan(R, g_acoustic_h_config[R], LH, nshots, 2, wave, bh, &plan));
+    FD_STAGE(s, plan.name);
+    AcousticHArgs a;
+    memset(&a, 0, sizeof(a));
+    a.wave = wave;
+    a.bcoef = bh;
+    a.dpx = dps;
+    a.dpy = dps + L.nx;
+    a.dpz = dps + L.nx + L.ny;
+    a.L = LH;
+    a.nshots = nshots;
+    a.lps = 2;
+    a.err = &dstats->flags;
+    const double ih2[3] = {1.0 / (grid->hx * grid->hx), 1.0 / (grid->hy * grid->hy),
+                           1.0 / (grid->hz * grid->hz)};
+    a.wc = (float)(gd.w[0] * (ih2[0] + ih2[1] + ih2[2]));
+    for (int k = 1; k <= R; ++k) {
+        a.wx[k] = (float)(gd.w[k] * ih2[0]);
+        a.wy[k] = (float)(gd.w[k] * ih2[1]);
+        a.wz[k] = (float)(gd.w[k] * ih2[2]);
+    }
+    SparseHArgs sp;
+    memset(&sp, 0, sizeof(sp));
+    sp.wave = wave;
+    sp.fields_per_shot = 2;
+    sp.L = LH;
+    sp.bcoef = bh;
+    sp.nshots = nshots;
+    sp.nt = nt;
+    sp.nsrc = nsrc;
+    sp.src_tab = src_tab;
+    sp.src_wav = swav.dev;
+    sp.nrec = nrec;
+    sp.rec_tab = rec_tab;
+    sp.rec_out = srec.dev;
+
+    // ---- time loop
+    const int nsteps = nt - 1;
+    const bool timing = stats_enabled();
+    const bool graphs = !timing && trace_level() < 2;
+    StepEvents evs;
+    if (timing) FD_TRY(evs.create(nsteps + 1, 3));
+    SideLane side;
+    const bool overlap = nrec > 0;
+    if (overlap) FD_TRY(side.begin());
+    auto step = [&](int i, int par, bool via_counter) -> fd_status {
+        AcousticHArgs ai = a;
+        ai.lev_cur = par;
+        ai.lev_prev = 1 - par;
+        ai.lev_out = 1 - par;
+        SparseHArgs si = sp;
+        si.inj_level = 1 - par;
+        si.rec_level = par;
+        si.step_base = via_counter ? counter : nullptr;
+        if (overlap) {
+            FD_TRY(side.fork(s));
+            FD_TRY(sparse_h_launch(si, i, false, true, side.get()));
+        }
+        if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 0), s));
+        FD_TRY(acoustic_h_launch(plan, ai, s));
+        if (!via_counter && trace_level() >= 2) FD_STAGE(s, "acoustic_step_h kernel");
+        if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 1), s));
+        FD_TRY(sparse_h_launch(si, i, nsrc > 0, false, s));
+        if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 2), s));
+        if (overlap) FD_TRY(side.join(s));
+        return FD_OK;
+    };
+    FD_TRY(run_time_loop(nsteps, s, counter, graphs, step,
+                         [&](int n) { return traces.upto(n, s); }));
+    const int last = nsteps & 1, prev_of_last = 1 - last;
+    {
+        SparseHArgs si = sp;
+        si.rec_level = last;
+        FD_TRY(sparse_h_launch(si, nt - 1, false, nrec > 0, s));
+    }
+    FD_TRY(check_finite_h(wave, LH, 2 * nshots, &dstats->flags, s));
+    FD_STAGE(s, "acoustic f16: time loop");
+
+    // ---- outputs: the stored values widened to FP32
+    if (u_final) {
+        for (int sh = 0; sh < nshots; ++sh) {
+            float *dst = sfinal.dev + (size_t)sh * 2 * dense;
+            FD_TRY(widen_rows(wave + (int64_t)(2 * sh + last) * LH.vol, LH.nxp, dst, L.nx, L.nx,
+                              rows, s));
+            FD_TRY(widen_rows(wave + (int64_t)(2 * sh + prev_of_last) * LH.vol, LH.nxp,
+                              dst + dense, L.nx, L.nx, rows, s));
+        }
+        FD_TRY(sfinal.copy_back(s));
+    }
+    if (traces.active())
+        FD_TRY(traces.finish(s));
+    else
+        FD_TRY(srec.copy_back(s));
+    FD_TRY(read_stats(dstats, &hs, s));
+    if (timing && nsteps > 0) {
+        double kms = 0.0, sms = 0.0;
+        for (int i = 0; i < nsteps; ++i) {
+            kms += evs.elapsed(i, 0, 1);
+            sms += evs.elapsed(i, 1, 2);
+        }
+        stats_add("acoustic_step_h", kms, nsteps, (double)dense * nshots);
+        stats_add("sparse", sms, nsteps, (double)(nrec + 8 * nsrc) * nshots);
+    }
+    ws.release();
+    FD_TRY(cs.finish());
+    return flags_to_status(hs.flags, "acoustic_forward_opts");
+}
+
 // ====================================================================== TTI
 
 static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt, int nshots,
@@ -1275,6 +1485,25 @@ fd_status acoustic_forward(const fd_grid *grid, int so, double dt, int nt, int n
                                           static_cast<cudaStream_t>(stream));
 }
 
+fd_status acoustic_forward_opts(const fd_grid *grid, int so, double dt, int nt, int nshots,
+                                const float *m, const float *damp, int nsrc,
+                                const float *src_xyz, const float *src_wav, int nrec,
+                                const float *rec_xyz, float *rec_out, const float *u_init,
+                                float *u_final, const fd_acoustic_options *opts, void *stream) {
+    fdsweep::clear_error();
+    const int storage = opts ? opts->storage : FD_STORAGE_F32;
+    if (storage == FD_STORAGE_F32)
+        return fdsweep::acoustic_forward_impl(grid, so, dt, nt, nshots, m, damp, nsrc, src_xyz,
+                                              src_wav, nrec, rec_xyz, rec_out, u_init, u_final,
+                                              (cudaStream_t)stream);
+    if (storage == FD_STORAGE_F16)
+        return fdsweep::acoustic_forward_h_impl(grid, so, dt, nt, nshots, m, damp, nsrc, src_xyz,
+                                                src_wav, nrec, rec_xyz, rec_out, u_init, u_final,
+                                                (cudaStream_t)stream);
+    return fdsweep::set_error(FD_ERR_ARG, "acoustic_forward_opts: storage %d not in {0, 1}",
+                              storage);
+}
+
 fd_status tti_forward(const fd_grid *grid, int so, double dt, int nt, int nshots, const float *m,
                       const float *damp, const float *epsilon, const float *delta,
                       const float *theta, const float *phi, int nsrc, const float *src_xyz,
@@ -1364,6 +1593,20 @@ fd_status fd_set_time_tiling(int so, int mode) {
 
 int fd_num_time_tiling_configs(int so) {
     return fdsweep::valid_so(so) ? fdsweep::acoustic2_num_configs(so / 2) : 0;
+}
+
+fd_status fd_set_acoustic_f16_config(int so, int config) {
+    if (!fdsweep::valid_so(so)) return fdsweep::set_error(FD_ERR_SO, "bad so %d", so);
+    const int r = so / 2;
+    if (config < -1 || config >= fdsweep::acoustic_h_num_configs(r))
+        return fdsweep::set_error(FD_ERR_ARG, "binary16 config %d out of range for so %d",
+                                  config, so);
+    fdsweep::g_acoustic_h_config[r] = config;
+    return FD_OK;
+}
+
+int fd_num_acoustic_f16_configs(int so) {
+    return fdsweep::valid_so(so) ? fdsweep::acoustic_h_num_configs(so / 2) : 0;
 }
 
 fd_status fd_set_acoustic_config(int so, int config) {

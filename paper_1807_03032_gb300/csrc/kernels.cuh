@@ -237,4 +237,63 @@ fd_status tti_fused_launch(const TtiPlan &plan, const TtiArgs &a, cudaStream_t s
 fd_status tti_launch(const TtiPlan &plan, const TtiArgs &a, cudaStream_t stream,
                      cudaEvent_t *ev /* 3 events or null */);
 
+// ---------------------------------------------------------------- binary16 storage
+
+// Reduced-precision storage (acoustic_h.cu): the wavefield levels and the
+// coefficient b are stored in IEEE binary16, the arithmetic is FP32.  Layout
+// [nbuf][nz][ny][nxp] halves with nxp = nx rounded up to a multiple of 8
+// (16-byte rows for TMA); raw binary16 bit patterns are held as half_bits.
+typedef unsigned short half_bits;
+
+struct AcousticHArgs {
+    half_bits *wave;          // lps buffers per shot: index shot * lps + level
+    const half_bits *bcoef;   // b = dt^2 / (m + damp dt / 2), binary16
+    const float *dpx, *dpy, *dpz;  // damp_d / dt per axis (FP32)
+    WaveLayout L;             // binary16 layout
+    int nshots;
+    int lps, lev_cur, lev_prev, lev_out;
+    float wc;
+    float wx[kMaxRadius + 1], wy[kMaxRadius + 1], wz[kMaxRadius + 1];
+    unsigned int *err;
+};
+
+int acoustic_h_num_configs(int radius);  // 0: no binary16 kernel for this radius
+fd_status acoustic_h_plan(int radius, int config, const WaveLayout &L, int nshots, int lps,
+                          half_bits *wave, const half_bits *bcoef, AcousticPlan *plan);
+fd_status acoustic_h_launch(const AcousticPlan &plan, const AcousticHArgs &args,
+                            cudaStream_t stream);
+
+// Sparse injection / interpolation on binary16 levels (forward schedule:
+// src[n] into level inj_level, rec[n] from level rec_level at step n).  The
+// injected value w_c b q is rounded to binary16 and added atomically (one
+// binary16 rounding of the sum).
+struct SparseHArgs {
+    half_bits *wave;
+    int fields_per_shot;
+    WaveLayout L;
+    const half_bits *bcoef;
+    int nshots, nt;
+    int nsrc;
+    const SparsePoint *src_tab;
+    const float *src_wav;
+    int inj_level;
+    int nrec;
+    const SparsePoint *rec_tab;
+    float *rec_out;
+    int rec_level;
+    const int *step_base;
+};
+fd_status sparse_h_launch(const SparseHArgs &a, int step, bool do_inject, bool do_interp,
+                          cudaStream_t stream);
+
+// dst row r (stride dst_stride halves) = nearest binary16 values of src row r
+// (stride src_stride floats), nx values per row, `rows` rows; and back.
+fd_status narrow_rows(const float *src, int64_t src_stride, half_bits *dst, int64_t dst_stride,
+                      int nx, int64_t rows, cudaStream_t stream);
+fd_status widen_rows(const half_bits *src, int64_t src_stride, float *dst, int64_t dst_stride,
+                     int nx, int64_t rows, cudaStream_t stream);
+// Sets DEV_ERR_NONFINITE in *flags if any value of the fields is inf or NaN.
+fd_status check_finite_h(const half_bits *field, const WaveLayout &L, int nfields,
+                         unsigned int *flags, cudaStream_t stream);
+
 }  // namespace fdsweep

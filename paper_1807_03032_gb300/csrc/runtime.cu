@@ -94,8 +94,9 @@ fd_status stats_get(const char *family, double *total_ms, int64_t *launches,
                     double *points_per_launch) {
     if (!family) return set_error(FD_ERR_ARG, "fd_stats_get: null family");
     std::lock_guard<std::mutex> lk(g_stats_mu);
-    static const char *known[] = {"acoustic_step", "acoustic_step2", "tti_pass1", "tti_pass2",
-                                  "tti_recompute", "tti_fused", "sparse"};
+    static const char *known[] = {"acoustic_step", "acoustic_step2", "acoustic_step_h",
+                                  "tti_pass1",     "tti_pass2",      "tti_recompute",
+                                  "tti_fused",     "sparse"};
     bool ok = false;
     for (const char *k : known) ok = ok || strcmp(k, family) == 0;
     if (!ok) return set_error(FD_ERR_ARG, "fd_stats_get: unknown family '%s'", family);
@@ -111,6 +112,17 @@ fd_status make_tensor_map_4d(CUtensorMap *map, const float *base, uint64_t nx, u
                              uint64_t nz, uint64_t nw, uint64_t stride_y_bytes,
                              uint64_t stride_z_bytes, uint64_t stride_w_bytes, uint32_t box_x,
                              uint32_t box_y, uint32_t box_z, uint32_t box_w) {
+    return make_tensor_map_4d_elem(map, base, 4, nx, ny, nz, nw, stride_y_bytes, stride_z_bytes,
+                                   stride_w_bytes, box_x, box_y, box_z, box_w);
+}
+
+fd_status make_tensor_map_4d_elem(CUtensorMap *map, const void *base, int elem_bytes,
+                                  uint64_t nx, uint64_t ny, uint64_t nz, uint64_t nw,
+                                  uint64_t stride_y_bytes, uint64_t stride_z_bytes,
+                                  uint64_t stride_w_bytes, uint32_t box_x, uint32_t box_y,
+                                  uint32_t box_z, uint32_t box_w) {
+    if (elem_bytes != 4 && elem_bytes != 2)
+        return set_error(FD_ERR_ARG, "tensor map: element size %d not supported", elem_bytes);
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     static std::once_flag once;
     static cudaError_t lookup_err = cudaSuccess;
@@ -129,7 +141,9 @@ fd_status make_tensor_map_4d(CUtensorMap *map, const float *base, uint64_t nx, u
     cuuint64_t strides[3] = {stride_y_bytes, stride_z_bytes, stride_w_bytes};
     cuuint32_t box[4] = {box_x, box_y, box_z, box_w};
     cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(base), dims,
+    const CUtensorMapDataType dtype =
+        elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    CUresult r = encode(map, dtype, 4, const_cast<void *>(base), dims,
                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

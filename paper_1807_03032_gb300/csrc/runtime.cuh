@@ -19,6 +19,13 @@ int trace_level();
 fd_status trace_stage(cudaStream_t s, const char *stage);
 #define FD_STAGE(stream, name) FD_TRY(::fdsweep::trace_stage((stream), (name)))
 
+// make_tensor_map_4d for 4-byte (FP32) or 2-byte (IEEE binary16) elements.
+fd_status make_tensor_map_4d_elem(CUtensorMap *map, const void *base, int elem_bytes,
+                                  uint64_t nx, uint64_t ny, uint64_t nz, uint64_t nw,
+                                  uint64_t stride_y_bytes, uint64_t stride_z_bytes,
+                                  uint64_t stride_w_bytes, uint32_t box_x, uint32_t box_y,
+                                  uint32_t box_z, uint32_t box_w);
+
 // True for device or managed memory (and for null); false for host memory.
 bool is_device_pointer(const void *p);
 

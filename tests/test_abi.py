@@ -51,6 +51,13 @@ def test_config_table_queries(lib):
     with pytest.raises(_native.FdError):
         _native.set_acoustic_config(8, 99)
     _native.set_acoustic_config(8, -1)
+    for so in (2, 4, 8, 12, 16):
+        assert _native.num_acoustic_f16_configs(so) >= 1
+    assert _native.num_acoustic_f16_configs(6) == 0
+    with pytest.raises(_native.FdError):
+        _native.set_acoustic_f16_config(8, 99)
+    _native.set_acoustic_f16_config(8, -1)
+    assert _native.stats_get("acoustic_step_h")[1] >= 0
 
 
 def test_stats_api(lib):

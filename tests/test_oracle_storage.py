@@ -149,3 +149,19 @@ def test_f16_storage_error_is_the_size_rounding_allows():
     bound = np.sqrt(nt) * 2.0 ** -12 / omega_dt
     assert 2.0 ** -12 < e < bound, (e, bound)
     assert rel(r1, r0) < bound
+
+
+def test_f16_step_is_the_stored_step_with_binary16_coefficient():
+    """One step of the f16 model equals one step with only b in binary16,
+    rounded through FP32 to binary16 (the two modes share everything else)."""
+    g, so, dt, _, m, src, wav, rec, damp, u0 = _problem(nt=2)
+    u0 = as_f16(u0).astype(np.float32)
+    _, uf = oracle.acoustic_forward_storage(g, so, dt, 2, m, src, wav[:, :2], rec, damp=damp,
+                                            u_init=u0, storage="f16")
+    _, uc = oracle.acoustic_forward_storage(g, so, dt, 2, m, src, wav[:, :2] * 0, rec,
+                                            damp=damp, u_init=u0, storage="f16_coef")
+    _, uz = oracle.acoustic_forward_storage(g, so, dt, 2, m, src, wav[:, :2] * 0, rec,
+                                            damp=damp, u_init=u0, storage="f16")
+    np.testing.assert_array_equal(uz[0, 0], as_f16(uc[0, 0].astype(np.float32)))
+    np.testing.assert_array_equal(uz[0, 1], uc[0, 1])
+    assert rel(uf[0, 0], uz[0, 0]) > 0  # the source shows with a nonzero wavelet
