@@ -423,6 +423,7 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     FD_CUDA_TRY(cudaMemsetAsync(bcoef, 0, (size_t)L.vol * 4, s));
     FD_TRY(init_medium_stats(dstats, s));
     FD_TRY(setup_acoustic_coeffs(sm.dev, sdamp.dev, dt, L, bcoef, dps, dstats, s));
+    FD_STAGE(s, "acoustic: coefficients");
     for (int sh = 0; sh < nshots; ++sh) {
         FD_TRY(setup_sparse_table(ssxyz.dev ? ssxyz.dev + (size_t)sh * nsrc * 3 : nullptr, nsrc,
                                   *grid, L, src_tab + (size_t)sh * nsrc, &dstats->flags, s));

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <chrono>
 #include <map>
 #include <mutex>
 #include <string>
@@ -169,11 +170,20 @@ fd_status trace_stage(cudaStream_t s, const char *stage) {
     fprintf(stderr, "[fdsweep] %s\n", stage);
     fflush(stderr);
     if (lvl >= 2) {
+        // host time from the previous synchronised stage to the end of this
+        // one (the stage's device work included)
+        thread_local std::chrono::steady_clock::time_point last;
         cudaError_t e = cudaStreamSynchronize(s);
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess)
             return set_error(FD_ERR_CUDA, "after stage '%s': %s", stage, cudaGetErrorString(e));
-        fprintf(stderr, "[fdsweep] %s: ok\n", stage);
+        const auto now = std::chrono::steady_clock::now();
+        const double ms =
+            last.time_since_epoch().count() == 0
+                ? 0.0
+                : std::chrono::duration<double, std::milli>(now - last).count();
+        last = now;
+        fprintf(stderr, "[fdsweep] %s: ok (+%.3f ms)\n", stage, ms);
         fflush(stderr);
     }
     return FD_OK;
