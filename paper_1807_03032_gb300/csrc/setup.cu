@@ -1,7 +1,8 @@
 // setup.cu -- K0: per-call coefficient precompute and validation.
 //
-//  * b = dt^2 / (m + damp dt / 2) per point (FP64 arithmetic, the reciprocal
-//    by Newton-Raphson, rounded once to FP32),
+//  * b = dt^2 / (m + damp dt / 2) per point, rounded once to FP32 (FP64
+//    arithmetic with a Newton-Raphson reciprocal where damp > 0, a two-float
+//    quotient with a residual correction where damp = 0),
 //    the factor that multiplies the Laplacian in the leapfrog update and the
 //    injected source (Listing finject's dt^2 q / m, generalised to the damped
 //    update); damping profiles scaled by 1/dt.
@@ -69,11 +70,33 @@ __device__ __forceinline__ double recip_newton(double x) {
     return y;
 }
 
+// The nearest float to (A + a) / x for FP32 A, a (|a| <= half a unit of A:
+// a two-float FP64 value) and x > 0, without FP64 arithmetic: the correctly
+// rounded quotient q = A / x is within one unit of the answer, and the exact
+// FMA residual of the quotient (Markstein's correction), A - q x, plus a,
+// tells which neighbour of q is nearest.  The sum with a is rounded once, so
+// the choice can differ from exact rounding only when the quotient lies
+// within about 2^-24 of a unit of a rounding midpoint.
+__device__ __forceinline__ float div_two_float_rn(float A, float a, float x) {
+    float q = __fdiv_rn(A, x);
+    const float r = fmaf(-q, x, A) + a;
+    const float up = __uint_as_float(__float_as_uint(q) + 1u) - q;  // spacing above q
+    const float dn = q - __uint_as_float(__float_as_uint(q) - 1u);  // spacing below q
+    if (r > 0.5f * up * x)
+        q += up;
+    else if (r < -0.5f * dn * x)
+        q -= dn;
+    return q;
+}
+
 // One grid row (j, k) per block iteration: the row index is split once per
-// row, not per point.
+// row, not per point.  Undamped points (damp = 0: the interior of the
+// absorbing border) take b = dt^2 / m from FP32 arithmetic
+// (div_two_float_rn, dt^2 = A + a); FP64 is slow on this part and is kept
+// for the damped points, where m + damp dt / 2 needs it.
 __global__ void acoustic_coeff_kernel(const float *__restrict__ m, const float *__restrict__ damp,
-                                      double dt, WaveLayout L, float *__restrict__ bcoef,
-                                      StatsKeys *stats) {
+                                      double dt, float dt2_hi, float dt2_lo, WaveLayout L,
+                                      float *__restrict__ bcoef, StatsKeys *stats) {
     const int64_t rows = (int64_t)L.ny * L.nz;
     const double dt2 = dt * dt;
     float lmin = __int_as_float(0x7f800000), lmax = 0.f;
@@ -86,12 +109,16 @@ __global__ void acoustic_coeff_kernel(const float *__restrict__ m, const float *
         float *brow = bcoef + (int64_t)k * L.plane + (int64_t)j * L.nxp;
         for (int i = threadIdx.x; i < L.nx; i += blockDim.x) {
             const float mv = mrow[i];
+            const float dxf = damp ? damp[i] : 0.f;
             double d = 0.0;
-            if (damp) d = (double)damp[i] + (double)dyf + (double)dzf;
+            if (damp) d = (double)dxf + (double)dyf + (double)dzf;
             if (!(mv > 0.f) || !isfinite(mv) || !(d >= 0.0) || !isfinite(d)) bad = DEV_ERR_MEDIUM;
             lmin = fminf(lmin, mv);
             lmax = fmaxf(lmax, mv);
-            brow[i] = (float)(dt2 * recip_newton((double)mv + 0.5 * d * dt));
+            if (dxf == 0.f && dyf == 0.f && dzf == 0.f && mv >= 1.17549435e-38f && mv <= 1.0e30f)
+                brow[i] = div_two_float_rn(dt2_hi, dt2_lo, mv);
+            else
+                brow[i] = (float)(dt2 * recip_newton((double)mv + 0.5 * d * dt));
         }
     }
     lmin = warp_min(lmin);
@@ -207,8 +234,11 @@ fd_status setup_acoustic_coeffs(const float *m, const float *damp, double dt,
                                 const WaveLayout &L, float *bcoef, float *dps,
                                 MediumStats *dev_stats, cudaStream_t stream) {
     StatsKeys *keys = reinterpret_cast<StatsKeys *>(dev_stats);
+    const double dt2 = dt * dt;
+    const float dt2_hi = (float)dt2;
+    const float dt2_lo = (float)(dt2 - (double)dt2_hi);
     acoustic_coeff_kernel<<<grid_for((int64_t)L.ny * L.nz * 256, 256), 256, 0, stream>>>(
-        m, damp, dt, L, bcoef, keys);
+        m, damp, dt, dt2_hi, dt2_lo, L, bcoef, keys);
     FD_CUDA_TRY(cudaGetLastError());
     note_launch(stream);
     const int nd = L.nx + L.ny + L.nz;

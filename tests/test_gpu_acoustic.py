@@ -285,3 +285,47 @@ def test_full_size_full_run_is_linear_in_the_source():
     assert float(torch.linalg.vector_norm(rec2 - 2 * rec1)) <= 1e-6 * float(
         torch.linalg.vector_norm(2 * rec1))
     assert w.nt == 594 and math.isclose(w.dt, 0.38 * 20.0 / 4.5)
+
+
+def test_injected_values_carry_the_correctly_rounded_b():
+    """From rest with unit wavelet samples, u^1 at each corner of a source is
+    exactly float32(float32(w_c) * b) with b the FP32 rounding of the FP64
+    value dt^2 / (m + damp dt / 2) -- for sources inside the absorbing border
+    (damped nodes) and inside the interior (undamped nodes) alike."""
+    torch = require_cuda()
+    import paper_1807_03032_gb300 as fd
+    n, h, nbl = 48, 10.0, 8
+    shape = (n, n, n)
+    rng = np.random.default_rng(21)
+    v = rng.uniform(1.5, 4.0, shape)
+    m = workloads.slowness_squared(v)
+    damp = workloads.damping_profile(shape, nbl, (h, h, h), 4.0)
+    dt = workloads.cfl_dt((h, h, h), 4.0)
+    # one source per 3 x 3 x 3 block of cells: no two share a node
+    cells = np.stack(np.meshgrid(*[np.arange(1, n - 2, 3)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    cells = cells[rng.permutation(len(cells))[:300]]
+    src = ((cells + rng.uniform(0.05, 0.95, cells.shape)) * h).astype(np.float32)[None]
+    wav = np.ones((1, 2, src.shape[1]), np.float32)
+    g = fd.Grid(shape, (h, h, h))
+    mt, dd, sx, sw = to_dev(torch, m, damp, src, wav)
+    e = torch.zeros((1, 0, 3), device="cuda")
+    _, uf = fd.acoustic_forward(g, 4, dt, 2, mt, sx, sw, e, damp=dd)
+    torch.cuda.synchronize()
+    u1 = uf[0, 0].cpu().numpy()
+    want = np.zeros(shape, np.float32)
+    dx, dy, dz = damp[:n].astype(np.float64), damp[n:2 * n].astype(np.float64), damp[2 * n:]
+    damped = 0
+    for p in src[0]:
+        s = p.astype(np.float64) / h
+        i1 = np.floor(s).astype(int)
+        fr = (s - i1).astype(np.float32)
+        for c in range(8):
+            ix, iy, iz = i1[0] + (c & 1), i1[1] + ((c >> 1) & 1), i1[2] + ((c >> 2) & 1)
+            w = [fr[a] if (c >> a) & 1 else np.float32(1) - fr[a] for a in range(3)]
+            cw = np.float32(np.float32(w[0] * w[1]) * w[2])
+            d = dx[ix] + dy[iy] + float(dz[iz])
+            damped += d > 0
+            b = np.float32(dt * dt / (float(m[iz, iy, ix]) + 0.5 * d * dt))
+            want[iz, iy, ix] = np.float32(cw * b)
+    assert 0 < damped < 8 * src.shape[1]
+    np.testing.assert_array_equal(u1, want)
