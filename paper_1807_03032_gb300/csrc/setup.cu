@@ -1,8 +1,8 @@
 // setup.cu -- K0: per-call coefficient precompute and validation.
 //
-//  * b = dt^2 / (m + damp dt / 2) per point, rounded once to FP32 (FP64
-//    arithmetic with a Newton-Raphson reciprocal where damp > 0, a two-float
-//    quotient with a residual correction where damp = 0),
+//  * b = dt^2 / (m + damp dt / 2) per point, rounded once to FP32 (two-float
+//    FP32 arithmetic with a residual-corrected quotient; FP64 with a
+//    Newton-Raphson reciprocal for points outside its range),
 //    the factor that multiplies the Laplacian in the leapfrog update and the
 //    injected source (Listing finject's dt^2 q / m, generalised to the damped
 //    update); damping profiles scaled by 1/dt.
@@ -70,33 +70,46 @@ __device__ __forceinline__ double recip_newton(double x) {
     return y;
 }
 
-// The nearest float to (A + a) / x for FP32 A, a (|a| <= half a unit of A:
-// a two-float FP64 value) and x > 0, without FP64 arithmetic: the correctly
-// rounded quotient q = A / x is within one unit of the answer, and the exact
-// FMA residual of the quotient (Markstein's correction), A - q x, plus a,
-// tells which neighbour of q is nearest.  The sum with a is rounded once, so
-// the choice can differ from exact rounding only when the quotient lies
-// within about 2^-24 of a unit of a rounding midpoint.
-__device__ __forceinline__ float div_two_float_rn(float A, float a, float x) {
-    float q = __fdiv_rn(A, x);
-    const float r = fmaf(-q, x, A) + a;
-    const float up = __uint_as_float(__float_as_uint(q) + 1u) - q;  // spacing above q
-    const float dn = q - __uint_as_float(__float_as_uint(q) - 1u);  // spacing below q
-    if (r > 0.5f * up * x)
-        q += up;
-    else if (r < -0.5f * dn * x)
-        q -= dn;
-    return q;
+// Two-float arithmetic (a value as an unevaluated sum hi + lo of floats),
+// with the error-free transformations TwoSum (Knuth) and TwoProduct (by FMA)
+// and the rounding-explicit intrinsics, so that no operation is contracted.
+struct TwoFloat {
+    float hi, lo;
+};
+
+__device__ __forceinline__ TwoFloat two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return TwoFloat{s, e};
+}
+
+// The nearest float to (A + a) / (X + x) for two-float numerator and
+// denominator (X > 0): q = A / X is within a few units of the answer; the
+// residual (A + a) - q (X + x), whose leading part A - q X is exact by FMA,
+// divided by X is the remaining correction, and q plus it is rounded once
+// (Markstein's final step).  The correction carries about 24 bits, so the
+// result can differ from exact rounding only when the quotient lies within
+// about 2^-44 of its size of a rounding midpoint.
+__device__ __forceinline__ float div_two_float_rn(float A, float a, float X, float x) {
+    const float q = __fdiv_rn(A, X);
+    float r = fmaf(-q, X, A);
+    r = __fadd_rn(r, a);
+    r = fmaf(-q, x, r);
+    return fmaf(r, __frcp_rn(X), q);
 }
 
 // One grid row (j, k) per block iteration: the row index is split once per
-// row, not per point.  Undamped points (damp = 0: the interior of the
-// absorbing border) take b = dt^2 / m from FP32 arithmetic
-// (div_two_float_rn, dt^2 = A + a); FP64 is slow on this part and is kept
-// for the damped points, where m + damp dt / 2 needs it.
+// row, not per point.  b = dt^2 / (m + (dx + dy + dz) dt / 2) is formed in
+// two-float FP32 arithmetic (dt^2 = A + a, dt / 2 = H + h): the damping sum
+// and its product with dt / 2 carried to about 2^-44, the quotient rounded
+// once (div_two_float_rn).  FP64 -- slow on this part -- remains for the
+// points that fail validation or lie outside the range where the two-float
+// steps are exact (m or a damping term negative, non-finite, or extreme).
 __global__ void acoustic_coeff_kernel(const float *__restrict__ m, const float *__restrict__ damp,
-                                      double dt, float dt2_hi, float dt2_lo, WaveLayout L,
-                                      float *__restrict__ bcoef, StatsKeys *stats) {
+                                      double dt, float dt2_hi, float dt2_lo, float hdt_hi,
+                                      float hdt_lo, WaveLayout L, float *__restrict__ bcoef,
+                                      StatsKeys *stats) {
     const int64_t rows = (int64_t)L.ny * L.nz;
     const double dt2 = dt * dt;
     float lmin = __int_as_float(0x7f800000), lmax = 0.f;
@@ -105,20 +118,32 @@ __global__ void acoustic_coeff_kernel(const float *__restrict__ m, const float *
         const int j = (int)(r % L.ny);
         const int k = (int)(r / L.ny);
         const float dyf = damp ? damp[L.nx + j] : 0.f, dzf = damp ? damp[L.nx + L.ny + k] : 0.f;
+        const bool row_ok = dyf >= 0.f && dyf <= 1.0e30f && dzf >= 0.f && dzf <= 1.0e30f;
         const float *mrow = m + r * L.nx;
         float *brow = bcoef + (int64_t)k * L.plane + (int64_t)j * L.nxp;
         for (int i = threadIdx.x; i < L.nx; i += blockDim.x) {
             const float mv = mrow[i];
             const float dxf = damp ? damp[i] : 0.f;
-            double d = 0.0;
-            if (damp) d = (double)dxf + (double)dyf + (double)dzf;
-            if (!(mv > 0.f) || !isfinite(mv) || !(d >= 0.0) || !isfinite(d)) bad = DEV_ERR_MEDIUM;
             lmin = fminf(lmin, mv);
             lmax = fmaxf(lmax, mv);
-            if (dxf == 0.f && dyf == 0.f && dzf == 0.f && mv >= 1.17549435e-38f && mv <= 1.0e30f)
-                brow[i] = div_two_float_rn(dt2_hi, dt2_lo, mv);
-            else
+            if (row_ok && dxf >= 0.f && dxf <= 1.0e30f && mv >= 1.17549435e-38f &&
+                mv <= 1.0e30f) {
+                // d = dx + dy + dz, eta = d dt / 2, x = m + eta, as two-floats
+                const TwoFloat s1 = two_sum(dxf, dyf);
+                const TwoFloat s2 = two_sum(s1.hi, dzf);
+                const float dlo = __fadd_rn(s1.lo, s2.lo);
+                const float ph = __fmul_rn(s2.hi, hdt_hi);
+                float pl = fmaf(s2.hi, hdt_hi, -ph);
+                pl = __fadd_rn(pl, __fadd_rn(__fmul_rn(s2.hi, hdt_lo), __fmul_rn(dlo, hdt_hi)));
+                const TwoFloat xs = two_sum(mv, ph);
+                brow[i] = div_two_float_rn(dt2_hi, dt2_lo, xs.hi, __fadd_rn(xs.lo, pl));
+            } else {
+                double d = 0.0;
+                if (damp) d = (double)dxf + (double)dyf + (double)dzf;
+                if (!(mv > 0.f) || !isfinite(mv) || !(d >= 0.0) || !isfinite(d))
+                    bad = DEV_ERR_MEDIUM;
                 brow[i] = (float)(dt2 * recip_newton((double)mv + 0.5 * d * dt));
+            }
         }
     }
     lmin = warp_min(lmin);
@@ -234,11 +259,11 @@ fd_status setup_acoustic_coeffs(const float *m, const float *damp, double dt,
                                 const WaveLayout &L, float *bcoef, float *dps,
                                 MediumStats *dev_stats, cudaStream_t stream) {
     StatsKeys *keys = reinterpret_cast<StatsKeys *>(dev_stats);
-    const double dt2 = dt * dt;
-    const float dt2_hi = (float)dt2;
-    const float dt2_lo = (float)(dt2 - (double)dt2_hi);
+    const double dt2 = dt * dt, hdt = 0.5 * dt;
+    const float dt2_hi = (float)dt2, hdt_hi = (float)hdt;
+    const float dt2_lo = (float)(dt2 - (double)dt2_hi), hdt_lo = (float)(hdt - (double)hdt_hi);
     acoustic_coeff_kernel<<<grid_for((int64_t)L.ny * L.nz * 256, 256), 256, 0, stream>>>(
-        m, damp, dt, dt2_hi, dt2_lo, L, bcoef, keys);
+        m, damp, dt, dt2_hi, dt2_lo, hdt_hi, hdt_lo, L, bcoef, keys);
     FD_CUDA_TRY(cudaGetLastError());
     note_launch(stream);
     const int nd = L.nx + L.ny + L.nz;
