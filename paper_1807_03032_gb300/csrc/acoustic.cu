@@ -28,6 +28,7 @@
 // point (read u^n, u^{n-1}, b; write u^{n+1}); halo and centre re-reads are
 // served by L2.
 #include <stdio.h>
+#include <string.h>
 
 #include "f32x2.cuh"
 #include "kernels.cuh"
@@ -58,6 +59,46 @@ struct AcCfg {
     static_assert(INT % 32 == 0 && THREADS % 32 == 0, "tile shape");
 };
 
+// Source injection by the CTA that wrote a source's corners, after its
+// column is complete: thread 0 adds w_c b q to each corner node inside the
+// column and z chunk, sources in order, with the sparse kernel's operations
+// (w_c = wx wy wz, times b, times q, added to the stored value).  The block
+// barrier before it makes the column's stores visible to thread 0; no other
+// CTA touches these nodes in this launch.  Out of line, with the column
+// recomputed from the block index, so that nothing stays live across the
+// plane loop for it.
+template <int BX, int BY>
+__device__ __noinline__ void inject_column(const AcousticStepArgs *a, const AcousticInject *inj,
+                                           int zchunk, int nzc) {
+    const int n = inj->step + (inj->step_base ? *inj->step_base : 0);
+    if (n < 0 || n >= inj->nt) return;
+    const int shot = blockIdx.z / nzc;
+    const int za = (blockIdx.z - shot * nzc) * zchunk;
+    const int zb = min(a->L.nz, za + zchunk);
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const int x1 = min(x0 + BX, a->L.nx), y1 = min(y0 + BY, a->L.ny);
+    float *u = a->wave + (int64_t)(shot * a->lps + a->lev_out) * a->L.vol;
+    for (int s = 0; s < inj->nsrc; ++s) {
+        const SparsePoint p = inj->src_tab[shot * inj->nsrc + s];
+        const int i = (int)(p.base % (uint32_t)a->L.nxp);
+        const int j = (int)((p.base / (uint32_t)a->L.nxp) % (uint32_t)a->L.ny);
+        const int k = (int)(p.base / (uint32_t)a->L.plane);
+        if (i + 1 < x0 || i >= x1 || j + 1 < y0 || j >= y1 || k + 1 < za || k >= zb) continue;
+        const float q = inj->src_wav[((int64_t)shot * inj->nt + n) * inj->nsrc + s];
+        for (int c = 0; c < 8; ++c) {
+            const int ci = i + (c & 1), cj = j + ((c >> 1) & 1), ck = k + ((c >> 2) & 1);
+            if (ci < x0 || ci >= x1 || cj < y0 || cj >= y1 || ck < za || ck >= zb) continue;
+            const float wx = (c & 1) ? p.fx : __fsub_rn(1.f, p.fx);
+            const float wy = (c & 2) ? p.fy : __fsub_rn(1.f, p.fy);
+            const float wz = (c & 4) ? p.fz : __fsub_rn(1.f, p.fz);
+            const int64_t off = (int64_t)ck * a->L.plane + (int64_t)cj * a->L.nxp + ci;
+            const float val =
+                __fmul_rn(__fmul_rn(__fmul_rn(__fmul_rn(wx, wy), wz), a->bcoef[off]), q);
+            u[off] = __fadd_rn(u[off], val);
+        }
+    }
+}
+
 // U: unroll factor of the plane loop.  The pending-output registers shift by
 // one plane per iteration; unrolling by U turns U - 1 of every U shifts into
 // register renaming instead of moves (U = 2R removes them all).
@@ -65,8 +106,9 @@ template <int R, int TX, int TY, int VY, int D, int U>
 __global__ void __launch_bounds__(TX *TY)
     acoustic_step_kernel(const __grid_constant__ CUtensorMap map_halo,
                          const __grid_constant__ CUtensorMap map_int,
-                         const __grid_constant__ CUtensorMap map_b, const AcousticStepArgs a,
-                         int zchunk, int nzc) {
+                         const __grid_constant__ CUtensorMap map_b,
+                         const __grid_constant__ AcousticStepArgs a,
+                         const __grid_constant__ AcousticInject inj, int zchunk, int nzc) {
     using C = AcCfg<R, TX, TY, VY, D>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *smem = reinterpret_cast<float *>(
@@ -300,6 +342,8 @@ __global__ void __launch_bounds__(TX *TY)
             if (jj >= 0)
                 mbar_wait_bounded(&full[jj % C::NSL], (uint32_t)((jj / C::NSL) & 1), 200000000ull);
     }
+    if (inj.nsrc > 0 && tid == 0 && !*abort_flag)
+        inject_column<C::BX, C::BY>(&a, &inj, zchunk, nzc);
 }
 
 struct ConfigEntry {
@@ -428,13 +472,21 @@ fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots,
 }
 
 fd_status acoustic_launch(const AcousticPlan &plan, const AcousticStepArgs &args,
-                          cudaStream_t stream) {
+                          cudaStream_t stream, const AcousticInject *inject) {
     int n = 0;
     const ConfigEntry *tab = config_table(plan.radius, &n);
     if (!tab || plan.config >= n) return set_error(FD_ERR_SO, "bad acoustic plan");
+    AcousticInject inj;
+    memset(&inj, 0, sizeof(inj));
+    if (inject && inject->nsrc > 0) {
+        if (inject->nsrc > kInjectMaxSources || args.slot_map)
+            return set_error(FD_ERR_ARG, "in-kernel injection: at most %d sources, no slot map",
+                             kInjectMaxSources);
+        inj = *inject;
+    }
     int zchunk = plan.zchunk, nzc = plan.nzc;
     void *params[] = {(void *)&plan.map_halo, (void *)&plan.map_int, (void *)&plan.map_b,
-                      (void *)&args, (void *)&zchunk, (void *)&nzc};
+                      (void *)&args, (void *)&inj, (void *)&zchunk, (void *)&nzc};
     FD_CUDA_TRY(cudaLaunchKernel(tab[plan.config].fn, plan.grid, plan.block, params, plan.smem,
                                  stream));
     note_launch(stream);

@@ -516,6 +516,11 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
         SideLane side;
         const bool overlap = nrec > 0;
         if (overlap) FD_TRY(side.begin());
+        // Up to kInjectMaxSources sources per shot are injected by the
+        // stencil kernel itself (the CTA that wrote the corners), which
+        // removes a dependent launch from every step; more go through the
+        // sparse kernel.
+        const bool inject_in_k1 = nsrc > 0 && nsrc <= kInjectMaxSources;
         auto step = [&](int i, int par, bool via_counter) -> fd_status {
             AcousticStepArgs ai = a;
             set_two_levels(ai, par);
@@ -523,15 +528,25 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
             si.inj_level0 = 1 - par;
             si.rec_level = par;
             si.step_base = via_counter ? counter : nullptr;
+            AcousticInject inj;
+            memset(&inj, 0, sizeof(inj));
+            if (inject_in_k1) {
+                inj.src_tab = src_tab;
+                inj.src_wav = swav.dev;
+                inj.nsrc = nsrc;
+                inj.nt = nt;
+                inj.step_base = si.step_base;
+                inj.step = i;
+            }
             if (overlap) {
                 FD_TRY(side.fork(s));
                 FD_TRY(sparse_launch(si, i, false, true, side.get()));
             }
             if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 0), s));
-            FD_TRY(acoustic_launch(plan, ai, s));
+            FD_TRY(acoustic_launch(plan, ai, s, &inj));
             if (!via_counter && trace_level() >= 2) FD_STAGE(s, "acoustic_step kernel");
             if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 1), s));
-            FD_TRY(sparse_launch(si, i, nsrc > 0, !overlap && nrec > 0, s));
+            FD_TRY(sparse_launch(si, i, nsrc > 0 && !inject_in_k1, !overlap && nrec > 0, s));
             if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 2), s));
             if (overlap) FD_TRY(side.join(s));
             return FD_OK;

@@ -72,6 +72,21 @@ inline void set_two_levels(AcousticStepArgs &a, int cur) {
     a.lev_out = 1 - cur;
 }
 
+// Source injection done by K1 itself (acoustic forward): src[n] is added
+// to u^{n+1} by the threads that write the source's trilinear corners, in
+// source order, with the operations of the sparse kernel (w_c b q added to
+// the stored value).  n = step + *step_base (step_base may be null).  At most
+// kInjectMaxSources sources per shot; nsrc = 0 disables it.
+constexpr int kInjectMaxSources = 16;
+
+struct AcousticInject {
+    const SparsePoint *src_tab;  // [nshots][nsrc]
+    const float *src_wav;        // [nshots][nt][nsrc]
+    int nsrc, nt;
+    const int *step_base;
+    int step;
+};
+
 int acoustic_num_configs(int radius);
 int acoustic_default_config(int radius);
 // `lps` levels per shot are addressable (buffers nshots * lps).  The launch
@@ -80,7 +95,7 @@ int acoustic_default_config(int radius);
 fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots, int lps,
                         float *wave, const float *bcoef, AcousticPlan *plan, int map_shots = 0);
 fd_status acoustic_launch(const AcousticPlan &plan, const AcousticStepArgs &args,
-                          cudaStream_t stream);
+                          cudaStream_t stream, const AcousticInject *inject = nullptr);
 
 // ---------------------------------------------------------------- time-tiled K1
 
