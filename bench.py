@@ -714,17 +714,20 @@ def cpu_baseline(w, so_list):
     cores = os.cpu_count() or 1
     t_total = 0.0
     pts = 0.0
+    per_so = {}
     for so in so_list:
         t0 = time.perf_counter()
         oracle.acoustic_forward(g, so, w.dt, 2, w.m, w.src_xyz, w.src_wav[:, :2], w.rec_xyz,
                                 damp=w.damp)
-        t_total += time.perf_counter() - t0
+        dt_so = time.perf_counter() - t0
+        t_total += dt_so
         pts += float(w.npoints)
+        per_so[str(so)] = round(float(w.npoints) / dt_so / 1e9, 4)
     out = {"value": round(pts / t_total / 1e9, 4), "unit": "GPts/s", "cores": cores,
            "kind": "oracle",
            "sample": f"1 time step at each so in {list(so_list)} of the {w.shape[0]}^3 workload "
                      "(FP64 C oracle, OpenMP over all host cores, setup included)",
-           "seconds": round(t_total, 2)}
+           "seconds": round(t_total, 2), "per_so": per_so}
     # the same oracle on one core, on a 256^3 sample of the workload recipe
     code = ("import json, time, oracle, workloads\n"
             "w = workloads.acoustic_large(n=256, so=4)\n"
