@@ -32,6 +32,7 @@
 
 #include "f32x2.cuh"
 #include "kernels.cuh"
+#include "runtime.cuh"
 
 namespace fdsweep {
 namespace {
@@ -430,8 +431,7 @@ fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots,
     plan->name = e.name;
     plan->smem = e.smem;
     plan->block = dim3(e.threads, 1, 1);
-    FD_CUDA_TRY(cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)e.smem));
+    FD_TRY(raise_smem_limit(e.fn, e.smem));
     int dev = 0, nsm = 0, per_sm = 0;
     FD_CUDA_TRY(cudaGetDevice(&dev));
     FD_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -458,9 +458,7 @@ fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots,
     plan->zchunk = zchunk;
     plan->nzc = nzc;
     plan->smem = e.smem + (size_t)zchunk * 4;
-    if (plan->smem > e.smem)
-        FD_CUDA_TRY(cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)plan->smem));
+    FD_TRY(raise_smem_limit(e.fn, plan->smem));
     FD_TRY(make_tensor_map_4d(&plan->map_halo, wave, L.nx, L.ny, L.nz, (uint64_t)map_shots * lps,
                               (uint64_t)L.nxp * 4, (uint64_t)L.plane * 4, (uint64_t)L.vol * 4,
                               e.pw, e.ph, 1, 1));

@@ -24,6 +24,7 @@
 // and extension re-reads are served by L2.
 #include "f32x2.cuh"
 #include "kernels.cuh"
+#include "runtime.cuh"
 
 namespace fdsweep {
 namespace {
@@ -426,8 +427,7 @@ fd_status acoustic2_plan(int radius, int config, const WaveLayout &L, int nshots
     plan->name = e.name;
     plan->smem = e.smem;
     plan->block = dim3(e.threads, 1, 1);
-    FD_CUDA_TRY(cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)e.smem));
+    FD_TRY(raise_smem_limit(e.fn, e.smem));
     int dev = 0, nsm = 0, per_sm = 0;
     FD_CUDA_TRY(cudaGetDevice(&dev));
     FD_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));

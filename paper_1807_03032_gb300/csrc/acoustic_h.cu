@@ -485,8 +485,7 @@ fd_status acoustic_h_plan(int radius, int config, const WaveLayout &L, int nshot
     int dev = 0, nsm = 0, per_sm = 0;
     FD_CUDA_TRY(cudaGetDevice(&dev));
     FD_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    FD_CUDA_TRY(cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)e.smem));
+    FD_TRY(raise_smem_limit(e.fn, e.smem));
     FD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, e.fn, e.threads, e.smem));
     if (per_sm < 1) return set_error(FD_ERR_CUDA, "kernel %s does not fit on an SM", e.name);
     const int ntx = (L.nx + e.bx - 1) / e.bx;
@@ -509,8 +508,7 @@ fd_status acoustic_h_plan(int radius, int config, const WaveLayout &L, int nshot
     plan->zchunk = zchunk;
     plan->nzc = nzc;
     plan->smem = e.smem + (size_t)zchunk * 4;
-    FD_CUDA_TRY(cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)plan->smem));
+    FD_TRY(raise_smem_limit(e.fn, plan->smem));
     const uint64_t sy = (uint64_t)L.nxp * 2, sz = (uint64_t)L.plane * 2, sw = (uint64_t)L.vol * 2;
     FD_TRY(make_tensor_map_4d_elem(&plan->map_halo, wave, 2, L.nx, L.ny, L.nz,
                                    (uint64_t)nshots * lps, sy, sz, sw, e.pw, e.ph, 1, 1));

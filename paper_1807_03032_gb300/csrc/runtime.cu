@@ -13,6 +13,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <utility>
 
 #include "runtime.cuh"
 
@@ -185,6 +186,21 @@ fd_status trace_stage(cudaStream_t s, const char *stage) {
         last = now;
         fprintf(stderr, "[fdsweep] %s: ok (+%.3f ms)\n", stage, ms);
         fflush(stderr);
+    }
+    return FD_OK;
+}
+
+fd_status raise_smem_limit(const void *fn, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> limit;
+    int dev = 0;
+    FD_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &cur = limit[std::make_pair(dev, fn)];
+    if (bytes > cur) {
+        FD_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes));
+        cur = bytes;
     }
     return FD_OK;
 }

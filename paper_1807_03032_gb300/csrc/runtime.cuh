@@ -26,6 +26,12 @@ fd_status make_tensor_map_4d_elem(CUtensorMap *map, const void *base, int elem_b
                                   uint64_t stride_w_bytes, uint32_t box_x, uint32_t box_y,
                                   uint32_t box_z, uint32_t box_w);
 
+// Raises a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes`, never lowering it: the limit belongs to the function and is
+// shared by every thread and call, so one call must not lower the limit
+// another call is about to launch with (concurrent calls from host threads).
+fd_status raise_smem_limit(const void *fn, size_t bytes);
+
 // True for device or managed memory (and for null); false for host memory.
 bool is_device_pointer(const void *p);
 

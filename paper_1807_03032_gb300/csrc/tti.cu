@@ -27,6 +27,7 @@
 // K2b one builds A = Hxy p and the other B = Hz r, they exchange A and B
 // through shared memory, and update p and r respectively.
 #include "kernels.cuh"
+#include "runtime.cuh"
 #include "tti_stencil.cuh"
 
 namespace fdsweep {
@@ -553,8 +554,8 @@ fd_status tti_plan(int radius, const WaveLayout &L, int nshots, float *wave, flo
     int dev = 0, nsm = 0, per_sm = 0;
     FD_CUDA_TRY(cudaGetDevice(&dev));
     FD_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    FD_CUDA_TRY(cudaFuncSetAttribute(in.p1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)in.smem1));
-    FD_CUDA_TRY(cudaFuncSetAttribute(in.p2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)in.smem2));
+    FD_TRY(raise_smem_limit(in.p1, in.smem1));
+    FD_TRY(raise_smem_limit(in.p2, in.smem2));
     FD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, in.p2, in.threads, in.smem2));
     if (per_sm < 1) return set_error(FD_ERR_CUDA, "TTI pass-2 kernel does not fit on an SM");
     const int ntx = (L.nx + in.bx - 1) / in.bx, nty = (L.ny + in.by - 1) / in.by;

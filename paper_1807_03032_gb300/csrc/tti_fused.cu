@@ -24,6 +24,7 @@
 // r-, b, a, s for the update, p+, r+ out: 48 bytes against 104 for the two
 // passes; the price is the gradient of the cross cells (1.6x the tile's).
 #include "kernels.cuh"
+#include "runtime.cuh"
 #include "tti_stencil.cuh"
 
 namespace fdsweep {
@@ -382,8 +383,7 @@ fd_status tti_fused_plan(int radius, int stag, const WaveLayout &L, int nshots, 
     FusedInfo in;
     if (!fused_info(radius, stag, config, &in))
         return set_error(FD_ERR_ARG, "the fused TTI scheme covers space orders up to 8");
-    FD_CUDA_TRY(cudaFuncSetAttribute(in.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)in.smem));
+    FD_TRY(raise_smem_limit(in.fn, in.smem));
     int dev = 0, nsm = 0, per_sm = 0;
     FD_CUDA_TRY(cudaGetDevice(&dev));
     FD_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));

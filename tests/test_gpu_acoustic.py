@@ -351,3 +351,54 @@ def test_colliding_sources_are_injected_in_order_bitwise():
     for rec, uf in outs[1:]:
         np.testing.assert_array_equal(uf, outs[0][1])
         np.testing.assert_array_equal(rec, outs[0][0])
+
+
+def test_concurrent_calls_from_host_threads_match_sequential_runs():
+    """Calls from several host threads (each on its own torch stream, device
+    and host buffers, graph-replayed time loops) give the same bits as the
+    same calls made one after another: the call state (private stream,
+    side lanes, workspace, error text) is per call and per thread."""
+    torch = require_cuda()
+    import threading
+    import paper_1807_03032_gb300 as fd
+    cases = []
+    for so, seed in ((4, 1), (8, 2), (8, 3), (4, 4)):
+        w, u_init = ragged_problem(so, nshots=1, nt=40, seed=seed)
+        separate_sources(w)
+        cases.append((w, u_init))
+
+    def run(w, u_init, host):
+        g = fd.Grid(w.shape, w.spacing, w.origin)
+        arrs = (w.m, w.src_xyz, w.src_wav, w.rec_xyz, w.damp, u_init)
+        if host:
+            m, sx, sw, rx, dd, ui = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                                     for a in arrs]
+        else:
+            m, sx, sw, rx, dd, ui = to_dev(torch, *arrs)
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            rec, uf = fd.acoustic_forward(g, w.so, w.dt, w.nt, m, sx, sw, rx, damp=dd, u_init=ui,
+                                          stream=stream.cuda_stream)
+        stream.synchronize()
+        return rec.cpu().numpy(), uf.cpu().numpy()
+
+    want = [run(w, u, host=(i % 2 == 1)) for i, (w, u) in enumerate(cases)]
+    got = [None] * len(cases)
+    errors = []
+
+    def worker(i):
+        try:
+            for _ in range(2):
+                got[i] = run(*cases[i], host=(i % 2 == 1))
+        except Exception as exc:  # reported below
+            errors.append(exc)
+
+    threads = [threading.Thread(target=worker, args=(i,)) for i in range(len(cases))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=300)
+    assert not errors, errors
+    for (rw, uw), (rg, ug) in zip(want, got):
+        np.testing.assert_array_equal(rg, rw)
+        np.testing.assert_array_equal(ug, uw)
