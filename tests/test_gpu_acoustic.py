@@ -402,3 +402,44 @@ def test_concurrent_calls_from_host_threads_match_sequential_runs():
     for (rw, uw), (rg, ug) in zip(want, got):
         np.testing.assert_array_equal(rg, rw)
         np.testing.assert_array_equal(ug, uw)
+
+
+@pytest.mark.parametrize("shape", [(3, 5, 7), (9, 2, 2), (2, 17, 3)])
+@pytest.mark.parametrize("so", [2, 8, 16])
+def test_grids_smaller_than_a_tile_and_the_stencil(shape, so):
+    """Grids smaller than one tile in every axis and thinner than the stencil
+    radius (most taps land on zero ghosts): FP32 storage against the oracle,
+    and one binary16 step against the storage model's rounding interval."""
+    torch = require_cuda()
+    import paper_1807_03032_gb300 as fd
+    h = (10.0, 12.0, 9.0)
+    rng = np.random.default_rng(sum(shape) + so)
+    m = workloads.slowness_squared(rng.uniform(1.5, 3.0, shape))
+    damp = rng.uniform(0.0, 0.05, shape[2] + shape[1] + shape[0]).astype(np.float32)
+    dt = 0.5 * workloads.cfl_dt(h, 3.0)
+    u0 = rng.uniform(-1.0, 1.0, (1, 2) + shape).astype(np.float16).astype(np.float32)
+    ext = np.array([(shape[2] - 1) * h[0], (shape[1] - 1) * h[1], (shape[0] - 1) * h[2]])
+    rec = (rng.uniform(0.0, 1.0, (1, 5, 3)) * ext).astype(np.float32)
+    src = (rng.uniform(0.0, 1.0, (1, 1, 3)) * ext).astype(np.float32)
+    nt = 12
+    wav = rng.standard_normal((1, nt, 1)).astype(np.float32)
+    g = fd.Grid(shape, h)
+    mt, dd, ui, sx, sw, rx = to_dev(torch, m, damp, u0, src, wav, rec)
+    r, uf = fd.acoustic_forward(g, so, dt, nt, mt, sx, sw, rx, damp=dd, u_init=ui)
+    torch.cuda.synchronize()
+    og = oracle.make_grid(shape, h)
+    ro, uo = oracle.acoustic_forward(og, so, dt, nt, m, src, wav, rec, damp=damp, u_init=u0)
+    assert rel_l2(uf.cpu().numpy(), uo) <= TOL
+    assert rel_l2(r.cpu().numpy(), ro) <= TOL
+    # binary16 storage, one step: a rounding of a value within the FP32 error
+    # bound of the exact step (the one-step check of tests/test_gpu_storage.py)
+    from tests.test_gpu_storage import check_stored_step, fp32_error_bound
+    e = torch.zeros((1, 0, 3), device="cuda")
+    _, uh = fd.acoustic_forward(g, so, dt, 2, mt, e, torch.zeros((1, 2, 0), device="cuda"), e,
+                                damp=dd, u_init=ui, storage="f16")
+    torch.cuda.synchronize()
+    ez = np.zeros((1, 0, 3), np.float32)
+    _, ux = oracle.acoustic_forward_storage(og, so, dt, 2, m, ez, np.zeros((1, 2, 0), np.float32),
+                                            ez, damp=damp, u_init=u0, storage="f16_coef")
+    check_stored_step(uh.cpu().numpy()[0, 0].astype(np.float64), ux[0, 0],
+                      fp32_error_bound(so, h, dt, m, u0), max_frac=0.05)
