@@ -239,13 +239,14 @@ def test_errors_are_reported():
 
 
 def test_full_size_parity_first_steps():
-    """512^3 (the benchmark's grid and launch configuration), so = 8 and 16:
-    four steps from a smooth random state with a source and the full
-    512 x 512 receiver plane, against the oracle at every point."""
+    """512^3 (the benchmark's grid and launch configuration), so = 4, 8, 12
+    and 16: four steps from a smooth random state with a source (injected by
+    the stencil kernel) and the full 512 x 512 receiver plane, against the
+    oracle at every point."""
     torch = require_cuda()
     import paper_1807_03032_gb300 as fd
     n = 512
-    for so in (8, 16):
+    for so in (4, 8, 12, 16):
         w = workloads.acoustic_large(n=n, so=so, nt=4)
         u_init = 0.01 * workloads.random_wavefields(w.shape, 21, sigma=6.0)
         g = fd.Grid(w.shape, w.spacing, w.origin)
