@@ -103,7 +103,7 @@ fd_status acoustic_forward(const fd_grid *grid, int so, double dt, int nt, int n
 /*
  * acoustic_forward_opts -- acoustic_forward with a choice of storage
  * precision.  The paper names mixed-precision arithmetic and on-the-fly data
- * compression as further performance work (section "Future work"); the step
+ * compression as further performance work (section "Further work"); the step
  * is memory bound, so halving the stored bytes per point is the lever.
  *
  *   opts->storage  FD_STORAGE_F32: FP32 storage, identical to acoustic_forward.

@@ -389,7 +389,7 @@ done:
  * ---- Reduced-precision storage ------------------------------------------
  *
  * The paper lists mixed-precision arithmetic and on-the-fly data compression
- * among its further performance work (section "Future work").  Reading used
+ * among its further performance work (section "Further work").  Reading used
  * here: the bulk fields are STORED in IEEE binary16 and all arithmetic stays
  * in FP32 on the device; the oracle models the storage exactly and keeps its
  * own arithmetic in FP64.  What is stored:

@@ -2,7 +2,7 @@
 // the wavefield levels u^n, u^{n-1} and the coefficient b = dt^2/(m + damp
 // dt/2) are stored in IEEE binary16, all arithmetic is FP32.  This is the
 // paper's further work on mixed-precision arithmetic and on-the-fly
-// compression (section "Future work"): it halves the bytes per point of a
+// compression (section "Further work"): it halves the bytes per point of a
 // memory-bound step.
 //
 // The kernel keeps K1's design (acoustic.cu): one CTA per BX x BY column

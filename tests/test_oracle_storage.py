@@ -1,6 +1,6 @@
 """Pins of the oracle's reduced-precision storage model (binary16 wavefields
 and coefficient; the paper's further work on mixed precision, section
-"Future work").
+"Further work").
 
 The rounding function is checked against numpy's own float16 conversion (an
 independent implementation of the same IEEE rounding), the b form of the
