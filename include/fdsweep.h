@@ -279,14 +279,22 @@ fd_status acoustic_gradient(const fd_grid *grid, int so, double dt, int nt, int 
  * cannot allow that: code running under a fixed device-memory budget decided
  * up front, a process whose device memory belongs to another allocator (a
  * framework's caching pool), or a service that must not hit out-of-memory in
- * the middle of a request.  This entry point computes exactly what
- * acoustic_forward computes but keeps the workspace in one fixed, file-scope
- * device array of FD_STATIC_SCRATCH_BYTES, so a call allocates nothing
- * (no cudaMalloc, cudaFree, stream, event or graph creation).
+ * the middle of a request.  This entry point runs acoustic_forward's
+ * schedule with the same kernels and launch configuration but keeps the
+ * workspace in one fixed, file-scope device array of FD_STATIC_SCRATCH_BYTES,
+ * so a call allocates nothing (no cudaMalloc, cudaFree, stream, event or
+ * graph creation).  With at most 16 sources per shot (injected by the stencil
+ * kernel in source order, as acoustic_forward does) the results are
+ * bit-identical to acoustic_forward's; with more, sources whose trilinear
+ * stencils share a node are added atomically in an unspecified order, and the
+ * two agree to FP32 rounding.
  *
  *  - Arguments, layouts and results are those of acoustic_forward, except
- *    that every pointer must be device memory (FD_ERR_ARG otherwise) and the
- *    work runs directly on `stream` (synchronised once at the end).
+ *    that every pointer must be device memory of the current device or
+ *    managed memory (FD_ERR_ARG otherwise) and the work runs directly on
+ *    `stream` (synchronised once at the end).  The grid checks are
+ *    acoustic_forward's (padded volume below 2^32 points, finite spacing and
+ *    origin), made before the scratch is sized.
  *  - A problem whose workspace, 4 * (2 nshots + 1) * nz * ny * nxp bytes
  *    (nxp = nx rounded up to a multiple of 4) plus its sparse tables, exceeds
  *    FD_STATIC_SCRATCH_BYTES is rejected with FD_ERR_ARG before any launch.
@@ -372,6 +380,36 @@ fd_status fd_stats_get(const char *family, double *total_ms, int64_t *launches,
 /* Number of kernel launches this library has enqueued since it was loaded
  * (a replayed CUDA graph counts each of its kernel nodes). */
 int64_t fd_launch_count(void);
+
+/*
+ * Limit of the acoustic stencil kernel's bounded pipeline waits, in
+ * nanoseconds (a stage of the shared-memory ring that is not filled, or not
+ * released, within the limit makes the kernel stop its column, let the copies
+ * it already issued land, and report FD_ERR_TIMEOUT).  ns <= 0 restores the
+ * built-in 2 s.  A failure-injection knob for tests: with ns = 1 every such
+ * wait is a single non-blocking test, so the waits give up on copies that are
+ * merely in flight, the call returns FD_ERR_TIMEOUT and the device stays
+ * usable (the copies already issued are still waited for, with their own
+ * limit, before a stopped kernel exits).  Process-wide; it
+ * applies to launches enqueued after the call (a CUDA graph keeps the limit it
+ * was captured with).
+ */
+fd_status fd_set_wait_limit_ns(int64_t ns);
+
+/*
+ * The FP32 Laplacian weights the acoustic kernels use for a grid and space
+ * order (Listing fd-1's compact second derivative of radius so/2 per axis,
+ * divided by h_d^2): *centre receives the sum over the axes of the centre
+ * weights, w[9 d + k] the weight of the offset +-k along axis d (x, y, z;
+ * k = 1 .. so/2; entries k = 0 and beyond so/2 are zero).  The weights are
+ * the FP32 roundings of the closed-form FP64 weights, except that the centre
+ * is the rounding of -2 times the sum of the neighbour weights and the
+ * residual of that rounding is moved into the neighbour weights (nearest taps
+ * first): in the device's weights, as in the exact ones, the Laplacian of a
+ * constant field is zero.  Host-only (no CUDA call); FD_ERR_SO / FD_ERR_ARG
+ * for a bad space order or grid.
+ */
+fd_status fd_stencil_weights(const fd_grid *grid, int so, float *centre, float *w /* [3][9] */);
 
 /*
  * Time tiling of acoustic_forward (loop blocking across the time dimension,

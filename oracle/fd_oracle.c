@@ -561,6 +561,7 @@ int ora_tti_operators_kind(const ora_grid *g, int so, int periodic, int deriv,
         if (st) goto done;
     }
     /* projection on the symmetry axis: proj = n . grad q */
+#pragma omp parallel for schedule(static)
     for (size_t p = 0; p < N; ++p) {
         double nx = sin(theta[p]) * cos(phi[p]), ny = sin(theta[p]) * sin(phi[p]),
                nz = cos(theta[p]);
@@ -571,6 +572,7 @@ int ora_tti_operators_kind(const ora_grid *g, int so, int periodic, int deriv,
     for (int a = 0; a < 3; ++a) {
         if (hz) {
             /* hz += D_a (n_a * proj) */
+#pragma omp parallel for schedule(static)
             for (size_t p = 0; p < N; ++p) {
                 double na = a == 0   ? sin(theta[p]) * cos(phi[p])
                             : a == 1 ? sin(theta[p]) * sin(phi[p])
@@ -578,11 +580,13 @@ int ora_tti_operators_kind(const ora_grid *g, int so, int periodic, int deriv,
                 tmp[p] = na * proj[p];
             }
             ora_first_derivative_kind(g, so, periodic, a, outer, tmp, dtmp);
+#pragma omp parallel for schedule(static)
             for (size_t p = 0; p < N; ++p) hz[p] += dtmp[p];
         }
         if (lq) {
             /* lq += D_a (D_a q) */
             ora_first_derivative_kind(g, so, periodic, a, outer, grad[a], dtmp);
+#pragma omp parallel for schedule(static)
             for (size_t p = 0; p < N; ++p) lq[p] += dtmp[p];
         }
     }
@@ -608,6 +612,7 @@ static void record(const ora_grid *g, int receiver, int nrec, const float *rxyz,
         return;
     }
     const size_t N = npts(g);
+#pragma omp parallel for schedule(static)
     for (size_t i = 0; i < N; ++i) tmp[i] = 0.5 * (p[i] + r[i]);
     ora_interpolate(g, nrec, rxyz, tmp, out);
 }
@@ -671,10 +676,12 @@ int ora_tti_forward_opts(const ora_grid *g, int so, int periodic, int deriv, int
             if (!st) st = ora_tti_operators_kind(g, so, periodic, deriv, th, ph, r, hzr, NULL);
             if (st) goto done;
             /* p equation: rhs = (1+2eps)(Lp - Hz p) + sqrt(1+2delta) Hz r */
+#pragma omp parallel for schedule(static)
             for (size_t i = 0; i < N; ++i)
                 rhs[i] = (1.0 + 2.0 * eps[i]) * (lp[i] - hzp[i]) + sqrt(1.0 + 2.0 * del[i]) * hzr[i];
             leapfrog(g, dt, m, damp, rhs, p, pm, pn);
             /* r equation: rhs = sqrt(1+2delta)(Lp - Hz p) + Hz r */
+#pragma omp parallel for schedule(static)
             for (size_t i = 0; i < N; ++i)
                 rhs[i] = sqrt(1.0 + 2.0 * del[i]) * (lp[i] - hzp[i]) + hzr[i];
             leapfrog(g, dt, m, damp, rhs, r, rm, rn);

@@ -29,7 +29,8 @@ EXPORTED = ("acoustic_forward", "tti_forward", "tti_forward_opts", "fd_last_erro
             "fd_engine_add_shot", "fd_engine_step", "fd_engine_shot_status", "fd_engine_release",
             "fd_engine_stream", "fd_engine_sync", "fd_engine_destroy", "fd_set_time_tiling",
             "fd_num_time_tiling_configs", "fd_set_tti_config", "fd_num_tti_configs",
-            "acoustic_forward_opts", "fd_set_acoustic_f16_config", "fd_num_acoustic_f16_configs")
+            "acoustic_forward_opts", "fd_set_acoustic_f16_config", "fd_num_acoustic_f16_configs",
+            "fd_stencil_weights", "fd_set_wait_limit_ns")
 
 
 class FdGrid(ctypes.Structure):
@@ -143,12 +144,26 @@ def load(path: str = LIB_PATH):
                      "fd_engine_step", "fd_engine_shot_status", "fd_engine_release",
                      "fd_engine_stream", "fd_engine_sync", "fd_engine_destroy", "fd_set_time_tiling",
             "fd_num_time_tiling_configs", "fd_set_tti_config", "fd_num_tti_configs",
-            "acoustic_forward_opts", "fd_set_acoustic_f16_config", "fd_num_acoustic_f16_configs"):
+            "acoustic_forward_opts", "fd_set_acoustic_f16_config", "fd_num_acoustic_f16_configs",
+            "fd_stencil_weights", "fd_set_wait_limit_ns"):
             getattr(lib, name).restype = I
+        FP = ctypes.POINTER(ctypes.c_float)
+        lib.fd_stencil_weights.argtypes = [G, I, FP, FP]
+        lib.fd_set_wait_limit_ns.argtypes = [ctypes.c_int64]
         lib.fd_launch_count.argtypes = []
         lib.fd_launch_count.restype = ctypes.c_int64
         _lib = lib
         return lib
+
+
+def stencil_weights(shape_zyx, spacing_xyz, so):
+    """(centre, w[3][9]): the FP32 Laplacian weights of the acoustic kernels."""
+    lib = load()
+    c = ctypes.c_float()
+    w = (ctypes.c_float * 27)()
+    check(lib.fd_stencil_weights(grid_struct(shape_zyx, spacing_xyz), int(so), ctypes.byref(c),
+                                 w))
+    return c.value, [[w[9 * d + k] for k in range(9)] for d in range(3)]
 
 
 def check(status: int):

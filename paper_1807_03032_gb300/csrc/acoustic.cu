@@ -111,6 +111,8 @@ __global__ void __launch_bounds__(TX *TY)
                          const __grid_constant__ AcousticStepArgs a,
                          const __grid_constant__ AcousticInject inj, int zchunk, int nzc) {
     using C = AcCfg<R, TX, TY, VY, D>;
+    // the divergence watchdog stopped the run: nothing more to compute
+    if (__ldcg(a.err) & DEV_ERR_NONFINITE) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *smem = reinterpret_cast<float *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
@@ -132,6 +134,7 @@ __global__ void __launch_bounds__(TX *TY)
     const int wcur = shot * a.lps + a.lev_cur, wprev = shot * a.lps + a.lev_prev;
     const int wout = shot * a.lps + a.lev_out;
     const int gx = x0 + 4 * tx;
+    const uint64_t wait_ns = a.wait_ns ? a.wait_ns : 2000000000ull;
 
     if (tid == 0) {
         prefetch_tensormap(&map_halo);
@@ -153,7 +156,7 @@ __global__ void __launch_bounds__(TX *TY)
     auto issue = [&](int jj) -> bool {
         const int slot = jj % C::NSL;
         if (jj >= C::NSL &&
-            !mbar_wait_bounded(&empty[slot], (uint32_t)(((jj - C::NSL) / C::NSL) & 1)))
+            !mbar_wait_bounded(&empty[slot], (uint32_t)(((jj - C::NSL) / C::NSL) & 1), wait_ns))
             return false;
         const bool with_out = jj >= 2 * R;
         mbar_arrive_expect_tx(&full[slot], C::HALO_BYTES + (with_out ? 3 * C::INT_BYTES : 0));
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(TX *TY)
             }
         }
         const int slot = j % C::NSL;
-        if (*abort_flag || !mbar_wait_bounded(&full[slot], (uint32_t)((j / C::NSL) & 1))) {
+        if (*abort_flag || !mbar_wait_bounded(&full[slot], (uint32_t)((j / C::NSL) & 1), wait_ns)) {
             *abort_flag = 1;
             atomicOr(a.err, DEV_ERR_TIMEOUT);
             break;
@@ -483,8 +486,10 @@ fd_status acoustic_launch(const AcousticPlan &plan, const AcousticStepArgs &args
         inj = *inject;
     }
     int zchunk = plan.zchunk, nzc = plan.nzc;
+    AcousticStepArgs a = args;
+    if (!a.wait_ns) a.wait_ns = wait_limit_ns();
     void *params[] = {(void *)&plan.map_halo, (void *)&plan.map_int, (void *)&plan.map_b,
-                      (void *)&args, (void *)&inj, (void *)&zchunk, (void *)&nzc};
+                      (void *)&a, (void *)&inj, (void *)&zchunk, (void *)&nzc};
     FD_CUDA_TRY(cudaLaunchKernel(tab[plan.config].fn, plan.grid, plan.block, params, plan.smem,
                                  stream));
     note_launch(stream);

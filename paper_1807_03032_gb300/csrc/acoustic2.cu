@@ -160,6 +160,7 @@ __global__ void __launch_bounds__(TX *TY)
                           const AcousticStep2Args a2, int zchunk, int nzc) {
     using C = T2Cfg<R, TX, TY, D>;
     const AcousticStepArgs &a = a2.s;
+    if (__ldcg(a.err) & DEV_ERR_NONFINITE) return;  // stopped by the divergence watchdog
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *smem = reinterpret_cast<float *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));

@@ -22,9 +22,7 @@ namespace fdsweep {
 
 fd_status finish_medium_stats(MediumStats *dev_stats, cudaStream_t stream);
 
-namespace {
-
-constexpr int kGraphChunk = 16;  // steps per captured graph (even: parity repeats)
+// ------------------------------------------------ numerics shared by every entry point
 
 // Central FD weights for radius r, closed form:
 //   second derivative w_k = 2 (-1)^{k+1} (r!)^2 / (k^2 (r-k)! (r+k)!), w_0 = -2 sum w_k
@@ -54,6 +52,86 @@ double second_symbol_max(int r, const double *w) {
     }
     return best;
 }
+
+double acoustic_dt_bound(const fd_grid &g, int r, double m_min) {
+    double w[kMaxRadius + 1] = {0.0}, c[kMaxRadius + 1] = {0.0};
+    fd_weights(r, w, c);
+    const double vmax = 1.0 / sqrt(m_min);
+    const double lam = second_symbol_max(r, w) *
+                       (1.0 / (g.hx * g.hx) + 1.0 / (g.hy * g.hy) + 1.0 / (g.hz * g.hz));
+    return 2.0 / (vmax * sqrt(lam));
+}
+
+// The FP32 weights sum to zero exactly, as the FP64 weights do (w_0 = -2 sum
+// w_k): the Laplacian of a constant is then zero in the device's weights too.
+// Rounding each weight to FP32 on its own leaves a residual of up to ~1e-7 of
+// the centre weight, which acts as a spurious mass term (the scheme solves
+// m u_tt = lap u + eps u) and shifts the phase of every wave coherently, by
+// about eps / (2 k^2) relative, so that the error grows linearly in time: on
+// the 1000 ms acoustic workload at so = 12 the FP32 run ended 1.1e-4 (relative
+// L2) from the FP64 scheme with independently rounded weights.  So the centre
+// weight is the FP32 rounding of -2 sum_k (wx_k + wy_k + wz_k) and what that
+// rounding leaves is moved into the neighbour weights, in the order of their
+// effect on the operator's second moment (tap k of axis d changes the k^2
+// coefficient by 2 k^2 h_d^2 per unit of weight: nearest taps of the finest
+// axes first), each by less than one ulp of the centre weight; the second
+// moment of every axis stays within 1e-6 of its exact value (a phase
+// velocity error below 5e-7).  The FP64 sums are exact while
+// the spacings differ by less than a factor of about 4 (48 FP32 terms whose
+// exponents then span under 24 bits); beyond that the residual left is at the
+// level of FP64 rounding.
+void laplacian_weights(const fd_grid &g, int r, float *wc, float *wx, float *wy, float *wz) {
+    double w[kMaxRadius + 1] = {0.0}, c[kMaxRadius + 1] = {0.0};
+    fd_weights(r, w, c);
+    const double ih2[3] = {1.0 / (g.hx * g.hx), 1.0 / (g.hy * g.hy), 1.0 / (g.hz * g.hz)};
+    float *wa[3] = {wx, wy, wz};
+    double sum = 0.0;  // 2 sum_k of the FP32 neighbour weights of all axes
+    for (int a = 0; a < 3; ++a) {
+        wa[a][0] = 0.f;  // the centre weights of all axes are in wc
+        for (int k = 1; k <= kMaxRadius; ++k) {
+            wa[a][k] = (float)(w[k] * ih2[a]);
+            sum += 2.0 * (double)wa[a][k];
+        }
+    }
+    *wc = (float)(-sum);
+    double residual = (double)*wc + sum;
+    // taps (axis, k) by increasing k^2 h_d^2
+    int order[3 * kMaxRadius];
+    int ntaps = 0;
+    for (int k = 1; k <= r; ++k)
+        for (int a = 0; a < 3; ++a) order[ntaps++] = a * (kMaxRadius + 1) + k;
+    auto impact = [&](int t) {
+        const int a = t / (kMaxRadius + 1), k = t % (kMaxRadius + 1);
+        return (double)k * k / ih2[a];
+    };
+    for (int i = 1; i < ntaps; ++i)  // insertion sort, stable
+        for (int j = i; j > 0 && impact(order[j]) < impact(order[j - 1]); --j) {
+            const int t = order[j];
+            order[j] = order[j - 1];
+            order[j - 1] = t;
+        }
+    for (int i = 0; i < ntaps && residual != 0.0; ++i) {
+        float &wt = wa[order[i] / (kMaxRadius + 1)][order[i] % (kMaxRadius + 1)];
+        const float old = wt;
+        wt = (float)((double)old - 0.5 * residual);
+        residual -= 2.0 * ((double)old - (double)wt);
+    }
+}
+
+WaveLayout wave_layout(const fd_grid &g) {
+    WaveLayout L;
+    L.nx = g.nx;
+    L.ny = g.ny;
+    L.nz = g.nz;
+    L.nxp = (g.nx + 3) / 4 * 4;
+    L.plane = (int64_t)L.nxp * g.ny;
+    L.vol = L.plane * g.nz;
+    return L;
+}
+
+namespace {
+
+constexpr int kGraphChunk = 16;  // steps per captured graph (even: parity repeats)
 
 // max over theta of the squared first-derivative symbol (2 sum c_k sin k theta)^2
 double first_symbol_sq_max(int r, const double *c) {
@@ -123,11 +201,10 @@ bool use_time_tiling(int R, int nsrc, int nsteps, int *config) {
     return mode > 0 || time_tiling_auto(R);
 }
 
-fd_status validate_common(const fd_grid *g, int so, double dt, int nt, int nshots, const float *m,
-                          int nsrc, const float *src_xyz, const float *src_wav, int nrec,
-                          const float *rec_xyz, const float *rec_out) {
+}  // namespace
+
+fd_status validate_grid(const fd_grid *g) {
     if (!g) return set_error(FD_ERR_ARG, "grid is null");
-    if (!valid_so(so)) return set_error(FD_ERR_SO, "space order %d not in {2,4,8,12,16}", so);
     if (g->nx < 2 || g->ny < 2 || g->nz < 2)
         return set_error(FD_ERR_ARG, "grid shape %d x %d x %d: every axis needs >= 2 points",
                          g->nx, g->ny, g->nz);
@@ -137,10 +214,22 @@ fd_status validate_common(const fd_grid *g, int so, double dt, int nt, int nshot
             return set_error(FD_ERR_ARG, "grid spacing must be finite and > 0");
         if (!isfinite(os[a])) return set_error(FD_ERR_ARG, "grid origin must be finite");
     }
-    const int64_t nxp = (g->nx + 3) / 4 * 4;
-    const int64_t vol = nxp * g->ny * (int64_t)g->nz;
-    if (vol >= (int64_t)1 << 32)
-        return set_error(FD_ERR_ARG, "grid of %lld padded points exceeds 2^32", (long long)vol);
+    // nxp * ny < 2^62 cannot overflow; the volume is formed only once the
+    // plane is known to be below 2^32 (so that it stays below 2^63)
+    const int64_t nxp = ((int64_t)g->nx + 3) / 4 * 4;
+    const int64_t plane = nxp * g->ny;
+    if (plane >= (int64_t)1 << 32 || plane * g->nz >= (int64_t)1 << 32)
+        return set_error(FD_ERR_ARG, "grid of %lld x %d x %d padded points reaches 2^32",
+                         (long long)nxp, g->ny, g->nz);
+    return FD_OK;
+}
+
+fd_status validate_common(const fd_grid *g, int so, double dt, int nt, int nshots, const float *m,
+                          int nsrc, const float *src_xyz, const float *src_wav, int nrec,
+                          const float *rec_xyz, const float *rec_out) {
+    if (!g) return set_error(FD_ERR_ARG, "grid is null");
+    if (!valid_so(so)) return set_error(FD_ERR_SO, "space order %d not in {2,4,8,12,16}", so);
+    FD_TRY(validate_grid(g));
     if (!(dt > 0.0) || !isfinite(dt)) return set_error(FD_ERR_ARG, "dt must be finite and > 0");
     if (nt < 1) return set_error(FD_ERR_ARG, "nt must be >= 1");
     if (nshots < 1) return set_error(FD_ERR_ARG, "nshots must be >= 1");
@@ -152,6 +241,12 @@ fd_status validate_common(const fd_grid *g, int so, double dt, int nt, int nshot
         return set_error(FD_ERR_ARG, "receivers given but rec_xyz or rec_out is null");
     return FD_OK;
 }
+
+int acoustic_step_config(int radius) {
+    return radius >= 0 && radius <= kMaxRadius ? g_acoustic_config[radius] : -1;
+}
+
+namespace {
 
 // An input array that may live on the host: device copy in the workspace.
 struct Staged {
@@ -168,7 +263,7 @@ struct Staged {
     }
     fd_status place(cudaStream_t s) {
         if (host)
-            FD_CUDA_TRY(cudaMemcpyAsync(dev, user, count * sizeof(float), cudaMemcpyHostToDevice, s));
+            FD_CUDA_TRY(cudaMemcpyAsync(dev, user, count * sizeof(float), cudaMemcpyDefault, s));
         return FD_OK;
     }
 };
@@ -189,7 +284,7 @@ struct StagedOut {
     }
     fd_status copy_back(cudaStream_t s) {
         if (host)
-            FD_CUDA_TRY(cudaMemcpyAsync(user, dev, count * sizeof(float), cudaMemcpyDeviceToHost, s));
+            FD_CUDA_TRY(cudaMemcpyAsync(user, dev, count * sizeof(float), cudaMemcpyDefault, s));
         return FD_OK;
     }
 };
@@ -218,7 +313,7 @@ struct TraceStreamer {
         FD_CUDA_TRY(cudaMemcpy2DAsync(out->user + (size_t)done * nrec, pitch,
                                       out->dev + (size_t)done * nrec, pitch,
                                       (size_t)(rows - done) * nrec * sizeof(float), nshots,
-                                      cudaMemcpyDeviceToHost, lane.get()));
+                                      cudaMemcpyDefault, lane.get()));
         done = rows;
         return FD_OK;
     }
@@ -351,17 +446,14 @@ struct StepEvents {
 
 struct GridDerived {
     WaveLayout L;
+    int R;
     double w[kMaxRadius + 1], c[kMaxRadius + 1];
 };
 
 GridDerived derive(const fd_grid *g, int so) {
     GridDerived d;
-    d.L.nx = g->nx;
-    d.L.ny = g->ny;
-    d.L.nz = g->nz;
-    d.L.nxp = (g->nx + 3) / 4 * 4;
-    d.L.plane = (int64_t)d.L.nxp * g->ny;
-    d.L.vol = d.L.plane * g->nz;
+    d.L = wave_layout(*g);
+    d.R = so / 2;
     for (int k = 0; k <= kMaxRadius; ++k) d.w[k] = d.c[k] = 0.0;
     fd_weights(so / 2, d.w, d.c);
     return d;
@@ -437,10 +529,7 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     FD_TRY(flags_to_status(hs.flags, "acoustic_forward"));
     {
         const double vmax = 1.0 / sqrt((double)hs.m_min);
-        const double sig = second_symbol_max(R, gd.w);
-        const double lam = sig * (1.0 / (grid->hx * grid->hx) + 1.0 / (grid->hy * grid->hy) +
-                                  1.0 / (grid->hz * grid->hz));
-        const double dt_max = 2.0 / (vmax * sqrt(lam));
+        const double dt_max = acoustic_dt_bound(*grid, R, (double)hs.m_min);
         if (dt > dt_max * (1.0 + 1e-12))
             return set_error(FD_ERR_CFL,
                              "dt = %.6g ms exceeds the leapfrog stability bound %.6g ms "
@@ -469,14 +558,7 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     a.L = L;
     a.nshots = nshots;
     a.err = &dstats->flags;
-    const double ih2[3] = {1.0 / (grid->hx * grid->hx), 1.0 / (grid->hy * grid->hy),
-                           1.0 / (grid->hz * grid->hz)};
-    a.wc = (float)(gd.w[0] * (ih2[0] + ih2[1] + ih2[2]));
-    for (int k = 1; k <= R; ++k) {
-        a.wx[k] = (float)(gd.w[k] * ih2[0]);
-        a.wy[k] = (float)(gd.w[k] * ih2[1]);
-        a.wz[k] = (float)(gd.w[k] * ih2[2]);
-    }
+    laplacian_weights(*grid, R, &a.wc, a.wx, a.wy, a.wz);
     SparseArgs sp;
     memset(&sp, 0, sizeof(sp));
     sp.wave = wave;
@@ -549,6 +631,8 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
             FD_TRY(sparse_launch(si, i, nsrc > 0 && !inject_in_k1, !overlap && nrec > 0, s));
             if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 2), s));
             if (overlap) FD_TRY(side.join(s));
+            if (i % kWatchEvery == kWatchEvery - 1)
+                FD_TRY(watchdog_launch(wave, L, lps * nshots, &dstats->flags, s));
             return FD_OK;
         };
         FD_TRY(run_time_loop(nsteps, s, counter, graphs, step,
@@ -600,6 +684,8 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
             sj.step_base = ai.step_base;
             FD_TRY(sparse_launch(sj, i, false, nrec > 0, s));
             if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 2), s));
+            if (i % (kWatchEvery / 2) == kWatchEvery / 2 - 1)
+                FD_TRY(watchdog_launch(wave, L, lps * nshots, &dstats->flags, s));
             return FD_OK;
         };
         FD_TRY(run_time_loop(npairs, s, counter, graphs, pair,
@@ -756,10 +842,7 @@ static fd_status acoustic_forward_h_impl(const fd_grid *grid, int so, double dt,
     FD_TRY(flags_to_status(hs.flags, "acoustic_forward_opts"));
     {
         const double vmax = 1.0 / sqrt((double)hs.m_min);
-        const double sig = second_symbol_max(R, gd.w);
-        const double lam = sig * (1.0 / (grid->hx * grid->hx) + 1.0 / (grid->hy * grid->hy) +
-                                  1.0 / (grid->hz * grid->hz));
-        const double dt_max = 2.0 / (vmax * sqrt(lam));
+        const double dt_max = acoustic_dt_bound(*grid, R, (double)hs.m_min);
         if (dt > dt_max * (1.0 + 1e-12))
             return set_error(FD_ERR_CFL,
                              "dt = %.6g ms exceeds the leapfrog stability bound %.6g ms "
@@ -788,14 +871,7 @@ static fd_status acoustic_forward_h_impl(const fd_grid *grid, int so, double dt,
     a.nshots = nshots;
     a.lps = 2;
     a.err = &dstats->flags;
-    const double ih2[3] = {1.0 / (grid->hx * grid->hx), 1.0 / (grid->hy * grid->hy),
-                           1.0 / (grid->hz * grid->hz)};
-    a.wc = (float)(gd.w[0] * (ih2[0] + ih2[1] + ih2[2]));
-    for (int k = 1; k <= R; ++k) {
-        a.wx[k] = (float)(gd.w[k] * ih2[0]);
-        a.wy[k] = (float)(gd.w[k] * ih2[1]);
-        a.wz[k] = (float)(gd.w[k] * ih2[2]);
-    }
+    laplacian_weights(*grid, R, &a.wc, a.wx, a.wy, a.wz);
     SparseHArgs sp;
     memset(&sp, 0, sizeof(sp));
     sp.wave = wave;
@@ -1074,6 +1150,8 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
         si.step_base = via_counter ? counter : nullptr;
         FD_TRY(sparse_launch(si, i, nsrc > 0, nrec > 0, s));
         if (timing) FD_CUDA_TRY(cudaEventRecord(evs.at(i, 3), s));
+        if (i % kWatchEvery == kWatchEvery - 1)
+            FD_TRY(watchdog_launch(wave, L, 4 * nshots, &dstats->flags, s));
         return FD_OK;
     };
     FD_TRY(run_time_loop(nsteps, s, counter, !timing && trace_level() < 2, step));
@@ -1145,11 +1223,7 @@ static fd_status acoustic_common_setup(const fd_grid *grid, int so, double dt, c
     MediumStats hs;
     FD_TRY(read_stats(dstats, &hs, s));
     FD_TRY(flags_to_status(hs.flags, what));
-    const double vmax = 1.0 / sqrt((double)hs.m_min);
-    const double sig = second_symbol_max(so / 2, gd.w);
-    const double lam = sig * (1.0 / (grid->hx * grid->hx) + 1.0 / (grid->hy * grid->hy) +
-                              1.0 / (grid->hz * grid->hz));
-    const double dt_max = 2.0 / (vmax * sqrt(lam));
+    const double dt_max = acoustic_dt_bound(*grid, so / 2, (double)hs.m_min);
     if (dt > dt_max * (1.0 + 1e-12))
         return set_error(FD_ERR_CFL, "%s: dt = %.6g ms exceeds the stability bound %.6g ms", what,
                          dt, dt_max);
@@ -1169,14 +1243,7 @@ static void fill_step_args(AcousticStepArgs &a, const fd_grid *grid, const GridD
     a.L = L;
     a.nshots = nshots;
     a.err = err;
-    const double ih2[3] = {1.0 / (grid->hx * grid->hx), 1.0 / (grid->hy * grid->hy),
-                           1.0 / (grid->hz * grid->hz)};
-    a.wc = (float)(gd.w[0] * (ih2[0] + ih2[1] + ih2[2]));
-    for (int k = 1; k <= kMaxRadius; ++k) {
-        a.wx[k] = (float)(gd.w[k] * ih2[0]);
-        a.wy[k] = (float)(gd.w[k] * ih2[1]);
-        a.wz[k] = (float)(gd.w[k] * ih2[2]);
-    }
+    laplacian_weights(*grid, gd.R, &a.wc, a.wx, a.wy, a.wz);
 }
 
 /*
@@ -1571,6 +1638,23 @@ fd_status acoustic_gradient(const fd_grid *grid, int so, double dt, int nt, int 
 const char *fd_last_error(void) { return fdsweep::last_error(); }
 
 int64_t fd_launch_count(void) { return fdsweep::launch_count(); }
+
+fd_status fd_set_wait_limit_ns(int64_t ns) {
+    fdsweep::clear_error();
+    fdsweep::set_wait_limit_ns(ns > 0 ? (uint64_t)ns : 0);
+    return FD_OK;
+}
+
+fd_status fd_stencil_weights(const fd_grid *grid, int so, float *centre, float *w) {
+    fdsweep::clear_error();
+    if (!centre || !w) return fdsweep::set_error(FD_ERR_ARG, "fd_stencil_weights: null output");
+    if (!fdsweep::valid_so(so))
+        return fdsweep::set_error(FD_ERR_SO, "space order %d not in {2,4,8,12,16}", so);
+    FD_TRY(fdsweep::validate_grid(grid));
+    const int K = fdsweep::kMaxRadius + 1;
+    fdsweep::laplacian_weights(*grid, so / 2, centre, w, w + K, w + 2 * K);
+    return FD_OK;
+}
 
 const char *fd_version(void) { return "fdsweep 0.1 (sm_103a)"; }
 

@@ -103,6 +103,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return done != 0;
 }
 
+// Non-blocking test of an mbarrier phase.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
 __device__ __forceinline__ uint64_t global_timer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -110,9 +123,12 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
 }
 
 // Bounded wait on an mbarrier phase: gives up after `limit_ns` nanoseconds
-// and returns false (the caller records DEV_ERR_TIMEOUT and unwinds).
+// and returns false (the caller records DEV_ERR_TIMEOUT and unwinds).  A
+// limit of 1 ns or less makes it a single non-blocking test (the
+// failure-injection setting of fd_set_wait_limit_ns).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
                                                   uint64_t limit_ns = 2000000000ull) {
+    if (limit_ns <= 1) return mbar_test_wait(bar, parity);
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
     uint32_t spins = 0;

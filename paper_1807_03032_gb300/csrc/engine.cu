@@ -91,16 +91,6 @@ __global__ void engine_sparse_kernel(const EngineSparseArgs e, int offset, int c
 
 __global__ void engine_bump(int *g, int by) { *g += by; }
 
-double symbol_max2(int r, const double *w) {
-    double best = 0.0;
-    for (int t = 0; t <= 4096; ++t) {
-        double s = w[0];
-        for (int k = 1; k <= r; ++k) s += 2.0 * w[k] * cos(k * M_PI * t / 4096.0);
-        if (-s > best) best = -s;
-    }
-    return best;
-}
-
 }  // namespace
 
 struct Engine {
@@ -152,17 +142,6 @@ static size_t engine_bytes(const WaveLayout &L, int max_slots, int max_nsrc, int
     return o;
 }
 
-static WaveLayout layout_of(const fd_grid *g) {
-    WaveLayout L;
-    L.nx = g->nx;
-    L.ny = g->ny;
-    L.nz = g->nz;
-    L.nxp = (g->nx + 3) / 4 * 4;
-    L.plane = (int64_t)L.nxp * L.ny;
-    L.vol = L.plane * L.nz;
-    return L;
-}
-
 static void destroy_engine(Engine *e) {
     if (!e) return;
     if (e->stream) cudaStreamSynchronize(e->stream);
@@ -178,11 +157,9 @@ static fd_status engine_create(const fd_grid *g, int so, double dt, const float 
                                const float *damp, int max_slots, int max_nsrc, int max_nrec,
                                Engine **out) {
     if (!g || !out || !m) return set_error(FD_ERR_ARG, "fd_engine_create: null argument");
-    if (!(so == 2 || so == 4 || so == 8 || so == 12 || so == 16))
-        return set_error(FD_ERR_SO, "space order %d not in {2,4,8,12,16}", so);
-    if (g->nx < 2 || g->ny < 2 || g->nz < 2 || !(g->hx > 0) || !(g->hy > 0) || !(g->hz > 0) ||
-        !(dt > 0) || max_slots < 1 || max_nsrc < 0 || max_nrec < 0)
-        return set_error(FD_ERR_ARG, "fd_engine_create: bad grid, dt or sizes");
+    FD_TRY(validate_common(g, so, dt, 1, 1, m, 0, nullptr, nullptr, 0, nullptr, nullptr));
+    if (max_slots < 1 || max_nsrc < 0 || max_nrec < 0)
+        return set_error(FD_ERR_ARG, "fd_engine_create: bad slot or sparse-point counts");
     if (!is_device_pointer(m) || (damp && !is_device_pointer(damp)))
         return set_error(FD_ERR_ARG, "fd_engine_create: m and damp must be device memory");
     Engine *e = new Engine();
@@ -190,7 +167,7 @@ static fd_status engine_create(const fd_grid *g, int so, double dt, const float 
     e->so = so;
     e->R = so / 2;
     e->dt = dt;
-    e->L = layout_of(g);
+    e->L = wave_layout(*g);
     e->max_slots = max_slots;
     e->max_nsrc = max_nsrc;
     e->max_nrec = max_nrec;
@@ -205,7 +182,7 @@ static fd_status engine_create(const fd_grid *g, int so, double dt, const float 
     if (ce != cudaSuccess) return fail(set_error(FD_ERR_CUDA, "stream: %s", cudaGetErrorString(ce)));
     size_t off[9];
     const size_t bytes = engine_bytes(e->L, max_slots, max_nsrc, max_nrec, off);
-    ce = cudaMalloc(&e->base, bytes);
+    ce = simulated_alloc_failure() ? cudaErrorMemoryAllocation : cudaMalloc(&e->base, bytes);
     if (ce != cudaSuccess) {
         cudaGetLastError();
         e->base = nullptr;
@@ -249,16 +226,7 @@ static fd_status engine_create(const fd_grid *g, int so, double dt, const float 
     ENGINE_CUDA(cudaStreamSynchronize(s));
     if (hs.flags & DEV_ERR_MEDIUM)
         return fail(set_error(FD_ERR_ARG, "fd_engine_create: need finite m > 0 and damp >= 0"));
-    double w[kMaxRadius + 1] = {0.0}, ratio = 1.0, sum = 0.0;
-    for (int k = 1; k <= e->R; ++k) {
-        ratio = ratio * (double)(e->R - k + 1) / (double)(e->R + k);
-        w[k] = 2.0 * ((k & 1) ? 1.0 : -1.0) * ratio / ((double)k * k);
-        sum += w[k];
-    }
-    w[0] = -2.0 * sum;
-    const double ih2[3] = {1.0 / (g->hx * g->hx), 1.0 / (g->hy * g->hy), 1.0 / (g->hz * g->hz)};
-    const double dt_max = 2.0 * sqrt((double)hs.m_min) /
-                          sqrt(symbol_max2(e->R, w) * (ih2[0] + ih2[1] + ih2[2]));
+    const double dt_max = acoustic_dt_bound(*g, e->R, (double)hs.m_min);
     if (dt > dt_max * (1.0 + 1e-12))
         return fail(set_error(FD_ERR_CFL, "dt = %.6g ms exceeds the stability bound %.6g ms", dt,
                               dt_max));
@@ -271,12 +239,7 @@ static fd_status engine_create(const fd_grid *g, int so, double dt, const float 
     e->args.L = e->L;
     e->args.err = &e->stats->flags;
     e->args.slot_map = e->slot_map;
-    e->args.wc = (float)(w[0] * (ih2[0] + ih2[1] + ih2[2]));
-    for (int k = 1; k <= e->R; ++k) {
-        e->args.wx[k] = (float)(w[k] * ih2[0]);
-        e->args.wy[k] = (float)(w[k] * ih2[1]);
-        e->args.wz[k] = (float)(w[k] * ih2[2]);
-    }
+    laplacian_weights(*g, e->R, &e->args.wc, e->args.wx, e->args.wy, e->args.wz);
 #undef ENGINE_TRY
 #undef ENGINE_CUDA
     *out = e;
@@ -436,7 +399,8 @@ fd_status fd_engine_footprint(const fd_grid *grid, int max_slots, int max_nsrc, 
     fdsweep::clear_error();
     if (!grid || !bytes || max_slots < 1 || max_nsrc < 0 || max_nrec < 0)
         return fdsweep::set_error(FD_ERR_ARG, "fd_engine_footprint: bad argument");
-    *bytes = (int64_t)fdsweep::engine_bytes(fdsweep::layout_of(grid), max_slots, max_nsrc,
+    FD_TRY(fdsweep::validate_grid(grid));
+    *bytes = (int64_t)fdsweep::engine_bytes(fdsweep::wave_layout(*grid), max_slots, max_nsrc,
                                             max_nrec, nullptr);
     return FD_OK;
 }

@@ -20,6 +20,9 @@ struct WaveLayout {
     int64_t vol;    // nz * plane
 };
 
+// Padded device layout of a grid (nxp = nx rounded up to a multiple of 4).
+WaveLayout wave_layout(const fd_grid &g);
+
 // Trilinear stencil of one sparse point: index of the (x1, y1, z1) corner in
 // the padded layout and the fractional offsets along each axis (computed in
 // FP64, stored rounded to FP32).
@@ -29,6 +32,38 @@ struct SparsePoint {
 };
 
 constexpr int kMaxRadius = 8;
+
+// ---------------------------------------------------------------- host numerics
+//
+// One definition, in api.cu, for every entry point (forward, adjoint,
+// gradient, the batch engine, the allocation-free call), so that their FD
+// weights, stability bounds and argument checks cannot drift apart.
+
+// Central FD weights for radius r, closed form (second derivative w[0..r],
+// first derivative c[0..r]).
+void fd_weights(int r, double *w, double *c);
+// max over theta of the second-derivative symbol -(w_0 + 2 sum w_k cos k theta)
+double second_symbol_max(int r, const double *w);
+// Exact constant-coefficient stability bound of the acoustic leapfrog with the
+// compact Laplacian of radius r: 2 / (v_max sqrt(sigma_max sum_d h_d^-2)),
+// v_max = 1/sqrt(m_min).
+double acoustic_dt_bound(const fd_grid &g, int r, double m_min);
+// Laplacian weights of radius r as the stencil kernels take them: the sum of
+// the centre weights over the axes (wc) and w_k / h_d^2 for k = 1..kMaxRadius
+// (zero beyond r and at k = 0).
+void laplacian_weights(const fd_grid &g, int r, float *wc, float *wx, float *wy, float *wz);
+// The grid alone: >= 2 points per axis, finite spacing > 0 and origin, padded
+// volume below 2^32 points (the sparse tables index it in 32 bits).
+fd_status validate_grid(const fd_grid *g);
+// Checks shared by the entry points: the grid (>= 2 points per axis, finite
+// spacing > 0 and origin, padded volume below 2^32 points, which the sparse
+// tables index in 32 bits), so, dt, nt >= 1, nshots >= 1, m and the sparse
+// arrays present when their counts are non-zero.
+fd_status validate_common(const fd_grid *g, int so, double dt, int nt, int nshots, const float *m,
+                          int nsrc, const float *src_xyz, const float *src_wav, int nrec,
+                          const float *rec_xyz, const float *rec_out);
+// K1 launch configuration acoustic_forward uses for a radius (-1: default).
+int acoustic_step_config(int radius);
 
 // ---------------------------------------------------------------- acoustic K1
 
@@ -49,7 +84,10 @@ struct AcousticStepArgs {
     const int *slot_map;
     float wc;             // sum over axes of w_0 / h_d^2
     float wx[kMaxRadius + 1], wy[kMaxRadius + 1], wz[kMaxRadius + 1];  // w_k / h_d^2
-    unsigned int *err;
+    unsigned int *err;    // device error bits; a launch that finds DEV_ERR_NONFINITE
+                          // set (by the watchdog) returns at once
+    uint64_t wait_ns;     // limit of the pipeline's bounded waits (0: 2 s); filled
+                          // in by acoustic_launch from fd_set_wait_limit_ns
 };
 
 struct AcousticPlan {
@@ -196,6 +234,19 @@ fd_status init_medium_stats(MediumStats *dev_stats, cudaStream_t stream);
 // Sets DEV_ERR_NONFINITE in *flags if any element of the field is not finite.
 fd_status check_finite(const float *field, const WaveLayout &L, int nfields,
                        unsigned int *flags, cudaStream_t stream);
+// Divergence watchdog of the time loops: checks every x row of every
+// kWatchStride-th y row of every kWatchStride-th z plane of `nfields`
+// consecutive fields (1/64 of the points) and sets DEV_ERR_NONFINITE in
+// *flags if one is not finite.  The stencil kernels launched after that
+// return at once, so a diverging run stops within one watchdog period
+// instead of running its whole time budget.
+constexpr int kWatchStride = 8;
+constexpr int kWatchEvery = 16;  // time steps between two watchdog launches
+fd_status watchdog_launch(const float *field, const WaveLayout &L, int nfields,
+                          unsigned int *flags, cudaStream_t stream);
+// Process-wide limit of the acoustic stencil kernel's bounded pipeline waits
+// (fd_set_wait_limit_ns); 0 = the built-in 2 s.
+uint64_t wait_limit_ns();
 
 // ---------------------------------------------------------------- TTI K2a/K2b
 

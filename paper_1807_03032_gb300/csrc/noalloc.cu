@@ -67,48 +67,35 @@ fd_status scratch_for_current_device(void **out) {
     return FD_OK;
 }
 
-// Bump layout inside the fixed array (256-byte aligned pieces).
+// Bump layout inside the fixed array (256-byte aligned pieces).  Sizes are
+// counted without overflow: a piece larger than the whole array saturates
+// `used` beyond the array's size, so an oversized request is rejected rather
+// than wrapped to a small number.
 struct Carve {
     char *base;
     size_t used = 0;
     template <class T>
-    T *take(size_t count) {
+    T *take(uint64_t count) {
+        const uint64_t cap = (uint64_t)FD_STATIC_SCRATCH_BYTES;
         used = (used + 255) / 256 * 256;
-        T *p = reinterpret_cast<T *>(base + used);
-        used += count * sizeof(T) > 0 ? count * sizeof(T) : 1;
+        T *p = reinterpret_cast<T *>(base + (used <= cap ? used : 0));
+        const uint64_t bytes = count <= cap / sizeof(T) ? count * sizeof(T) : cap + 1;
+        used = used <= cap ? used + (bytes > 0 ? bytes : 1) : used;
         return p;
     }
 };
 
+// Counts are non-negative ints and vol < 2^32 (checked first), so every
+// product below fits in 64 bits.
 size_t needed_bytes(const WaveLayout &L, int nshots, int nsrc, int nrec) {
     Carve c{nullptr};
-    c.take<float>((size_t)2 * nshots * L.vol);
-    c.take<float>(L.vol);
-    c.take<float>(L.nx + L.ny + L.nz);
-    c.take<SparsePoint>((size_t)nshots * nsrc);
-    c.take<SparsePoint>((size_t)nshots * nrec);
+    c.take<float>((uint64_t)2 * nshots * (uint64_t)L.vol);
+    c.take<float>((uint64_t)L.vol);
+    c.take<float>((uint64_t)L.nx + L.ny + L.nz);
+    c.take<SparsePoint>((uint64_t)nshots * nsrc);
+    c.take<SparsePoint>((uint64_t)nshots * nrec);
     c.take<MediumStats>(1);
     return c.used;
-}
-
-void weights(int r, double *w) {
-    double ratio = 1.0, sum = 0.0;
-    for (int k = 1; k <= r; ++k) {
-        ratio = ratio * (double)(r - k + 1) / (double)(r + k);
-        w[k] = 2.0 * ((k & 1) ? 1.0 : -1.0) * ratio / ((double)k * k);
-        sum += w[k];
-    }
-    w[0] = -2.0 * sum;
-}
-
-double symbol_max(int r, const double *w) {
-    double best = 0.0;
-    for (int t = 0; t <= 4096; ++t) {
-        double s = w[0];
-        for (int k = 1; k <= r; ++k) s += 2.0 * w[k] * cos(k * M_PI * t / 4096.0);
-        if (-s > best) best = -s;
-    }
-    return best;
 }
 
 fd_status flags_status(unsigned int f) {
@@ -124,29 +111,17 @@ fd_status noalloc_impl(const fd_grid *g, int so, double dt, int nt, int nshots, 
                        const float *damp, int nsrc, const float *src_xyz, const float *src_wav,
                        int nrec, const float *rec_xyz, float *rec_out, const float *u_init,
                        float *u_final, cudaStream_t s) {
-    if (!g) return set_error(FD_ERR_ARG, "grid is null");
-    if (!(so == 2 || so == 4 || so == 8 || so == 12 || so == 16))
-        return set_error(FD_ERR_SO, "space order %d not in {2,4,8,12,16}", so);
-    if (g->nx < 2 || g->ny < 2 || g->nz < 2 || !(g->hx > 0) || !(g->hy > 0) || !(g->hz > 0) ||
-        !isfinite(g->hx) || !isfinite(g->hy) || !isfinite(g->hz))
-        return set_error(FD_ERR_ARG, "bad grid (every axis >= 2 points, finite spacing > 0)");
-    if (!(dt > 0.0) || !isfinite(dt) || nt < 1 || nshots < 1 || nsrc < 0 || nrec < 0 || !m)
-        return set_error(FD_ERR_ARG, "bad dt, nt, nshots, nsrc, nrec or null m");
-    if ((nsrc > 0 && (!src_xyz || !src_wav)) || (nrec > 0 && (!rec_xyz || !rec_out)))
-        return set_error(FD_ERR_ARG, "null source or receiver array");
+    FD_TRY(validate_common(g, so, dt, nt, nshots, m, nsrc, src_xyz, src_wav, nrec, rec_xyz,
+                           rec_out));
     for (const void *p : {(const void *)m, (const void *)damp, (const void *)src_xyz,
                           (const void *)src_wav, (const void *)rec_xyz, (const void *)rec_out,
                           (const void *)u_init, (const void *)u_final})
         if (p && !is_device_pointer(p))
-            return set_error(FD_ERR_ARG, "acoustic_forward_noalloc takes device pointers only");
+            return set_error(FD_ERR_ARG,
+                             "acoustic_forward_noalloc takes device pointers of the current "
+                             "device only");
     const int R = so / 2;
-    WaveLayout L;
-    L.nx = g->nx;
-    L.ny = g->ny;
-    L.nz = g->nz;
-    L.nxp = (g->nx + 3) / 4 * 4;
-    L.plane = (int64_t)L.nxp * L.ny;
-    L.vol = L.plane * L.nz;
+    const WaveLayout L = wave_layout(*g);
     const size_t need = needed_bytes(L, nshots, nsrc, nrec);
     if (need > (size_t)FD_STATIC_SCRATCH_BYTES)
         return set_error(FD_ERR_ARG,
@@ -180,11 +155,7 @@ fd_status noalloc_impl(const fd_grid *g, int so, double dt, int nt, int nshots, 
     FD_CUDA_TRY(cudaMemcpyAsync(&hs, dstats, sizeof(hs), cudaMemcpyDeviceToHost, s));
     FD_CUDA_TRY(cudaStreamSynchronize(s));
     FD_TRY(flags_status(hs.flags));
-    double w[kMaxRadius + 1] = {0.0};
-    weights(R, w);
-    const double ih2[3] = {1.0 / (g->hx * g->hx), 1.0 / (g->hy * g->hy), 1.0 / (g->hz * g->hz)};
-    const double dt_max = 2.0 / (sqrt(symbol_max(R, w) * (ih2[0] + ih2[1] + ih2[2])) /
-                                 sqrt((double)hs.m_min));
+    const double dt_max = acoustic_dt_bound(*g, R, (double)hs.m_min);
     if (dt > dt_max * (1.0 + 1e-12))
         return set_error(FD_ERR_CFL, "dt = %.6g ms exceeds the stability bound %.6g ms", dt, dt_max);
 
@@ -199,7 +170,7 @@ fd_status noalloc_impl(const fd_grid *g, int so, double dt, int nt, int nshots, 
                                               (size_t)L.ny * L.nz, cudaMemcpyDeviceToDevice, s));
 
     AcousticPlan plan;
-    FD_TRY(acoustic_plan(R, -1, L, nshots, 2, wave, bcoef, &plan));
+    FD_TRY(acoustic_plan(R, acoustic_step_config(R), L, nshots, 2, wave, bcoef, &plan));
     AcousticStepArgs a;
     memset(&a, 0, sizeof(a));
     a.wave = wave;
@@ -210,12 +181,7 @@ fd_status noalloc_impl(const fd_grid *g, int so, double dt, int nt, int nshots, 
     a.L = L;
     a.nshots = nshots;
     a.err = &dstats->flags;
-    a.wc = (float)(w[0] * (ih2[0] + ih2[1] + ih2[2]));
-    for (int k = 1; k <= R; ++k) {
-        a.wx[k] = (float)(w[k] * ih2[0]);
-        a.wy[k] = (float)(w[k] * ih2[1]);
-        a.wz[k] = (float)(w[k] * ih2[2]);
-    }
+    laplacian_weights(*g, R, &a.wc, a.wx, a.wy, a.wz);
     SparseArgs sp;
     memset(&sp, 0, sizeof(sp));
     sp.wave = wave;
@@ -236,12 +202,24 @@ fd_status noalloc_impl(const fd_grid *g, int so, double dt, int nt, int nshots, 
     sp.rec_tab = rec_tab;
     sp.rec_out = rec_out;
     sp.step_base = nullptr;
+    // the schedule of acoustic_forward: up to kInjectMaxSources sources per
+    // shot are injected by the stencil kernel itself, in source order
+    const bool inject_in_k1 = nsrc > 0 && nsrc <= kInjectMaxSources;
+    AcousticInject inj;
+    memset(&inj, 0, sizeof(inj));
+    if (inject_in_k1) {
+        inj.src_tab = src_tab;
+        inj.src_wav = src_wav;
+        inj.nsrc = nsrc;
+        inj.nt = nt;
+    }
     for (int n = 0; n + 1 < nt; ++n) {
         set_two_levels(a, n & 1);
-        FD_TRY(acoustic_launch(plan, a, s));
+        inj.step = n;
+        FD_TRY(acoustic_launch(plan, a, s, &inj));
         sp.inj_level0 = 1 - (n & 1);
         sp.rec_level = n & 1;
-        FD_TRY(sparse_launch(sp, n, nsrc > 0, nrec > 0, s));
+        FD_TRY(sparse_launch(sp, n, nsrc > 0 && !inject_in_k1, nrec > 0, s));
     }
     const int last = (nt - 1) & 1;
     sp.rec_level = last;

@@ -213,7 +213,15 @@ bool is_device_pointer(const void *p) {
         cudaGetLastError();
         return false;
     }
-    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+    if (attr.type == cudaMemoryTypeManaged) return true;
+    if (attr.type != cudaMemoryTypeDevice) return false;
+    // device memory of another GPU is not this call's to dereference
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.device == dev;
 }
 
 // ------------------------------------------------------------------ workspace
@@ -226,6 +234,20 @@ void Workspace::add_raw(void **slot, size_t bytes) {
     *slot = nullptr;
     total_ += bytes > 0 ? bytes : 1;
 }
+
+// ------------------------------------------------------------------ fault injection
+
+bool simulated_alloc_failure() {
+    const char *v = getenv("FDSWEEP_FAIL_ALLOC");
+    return v && v[0] == '1';
+}
+
+namespace {
+std::atomic<uint64_t> g_wait_limit_ns{0};
+}  // namespace
+
+uint64_t wait_limit_ns() { return g_wait_limit_ns.load(std::memory_order_relaxed); }
+void set_wait_limit_ns(uint64_t ns) { g_wait_limit_ns.store(ns, std::memory_order_relaxed); }
 
 fd_status Workspace::allocate(cudaStream_t s) {
     stream_ = s;
@@ -244,7 +266,8 @@ fd_status Workspace::allocate(cudaStream_t s) {
         cudaGetLastError();
     });
     if (total_ == 0) return FD_OK;
-    cudaError_t e = cudaMallocAsync(&base_, total_, s);
+    cudaError_t e = simulated_alloc_failure() ? cudaErrorMemoryAllocation
+                                              : cudaMallocAsync(&base_, total_, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         base_ = nullptr;

@@ -32,7 +32,17 @@ fd_status make_tensor_map_4d_elem(CUtensorMap *map, const void *base, int elem_b
 // another call is about to launch with (concurrent calls from host threads).
 fd_status raise_smem_limit(const void *fn, size_t bytes);
 
-// True for device or managed memory (and for null); false for host memory.
+// Host-side fault injection for tests: with the environment variable
+// FDSWEEP_FAIL_ALLOC=1 every device allocation of the library (per-call
+// workspaces, batch engines) fails as if the device were out of memory, and
+// the call returns FD_ERR_OOM without launching anything.
+bool simulated_alloc_failure();
+void set_wait_limit_ns(uint64_t ns);
+
+// True for managed memory, for device memory of the current device and for
+// null; false for host memory and for another device's memory (which the
+// entry points that accept host buffers stage like host memory, and the
+// device-only entry points reject).
 bool is_device_pointer(const void *p);
 
 // One stream-ordered device allocation per call, carved into 256-byte aligned

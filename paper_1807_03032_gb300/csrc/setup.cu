@@ -235,6 +235,26 @@ __global__ void finite_kernel(const float *__restrict__ f, int64_t n, unsigned i
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, DEV_ERR_NONFINITE);
 }
 
+// One thread per element of the sampled rows (see watchdog_launch).
+__global__ void watchdog_kernel(const float *__restrict__ f, WaveLayout L, int nfields, int nzs,
+                                int nys, unsigned int *flags) {
+    const int64_t per_field = (int64_t)nzs * nys * L.nxp;
+    const int64_t n = per_field * nfields;
+    bool bad = false;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t fld = p / per_field;
+        const int64_t r = p - fld * per_field;
+        const int64_t row = r / L.nxp;
+        const int x = (int)(r - row * L.nxp);
+        const int zi = (int)(row / nys), yi = (int)(row - (int64_t)zi * nys);
+        const int64_t off = fld * L.vol + (int64_t)zi * kWatchStride * L.plane +
+                            (int64_t)yi * kWatchStride * L.nxp + x;
+        if (!isfinite(f[off])) bad = true;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, DEV_ERR_NONFINITE);
+}
+
 int grid_for(int64_t n, int threads) {
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
@@ -298,6 +318,17 @@ fd_status check_finite(const float *field, const WaveLayout &L, int nfields, uns
                        cudaStream_t stream) {
     const int64_t n = L.vol * nfields;
     finite_kernel<<<grid_for(n, 256), 256, 0, stream>>>(field, n, flags);
+    FD_CUDA_TRY(cudaGetLastError());
+    note_launch(stream);
+    return FD_OK;
+}
+
+fd_status watchdog_launch(const float *field, const WaveLayout &L, int nfields,
+                          unsigned int *flags, cudaStream_t stream) {
+    const int nzs = (L.nz + kWatchStride - 1) / kWatchStride;
+    const int nys = (L.ny + kWatchStride - 1) / kWatchStride;
+    const int64_t n = (int64_t)nzs * nys * L.nxp * nfields;
+    watchdog_kernel<<<grid_for(n, 256), 256, 0, stream>>>(field, L, nfields, nzs, nys, flags);
     FD_CUDA_TRY(cudaGetLastError());
     note_launch(stream);
     return FD_OK;

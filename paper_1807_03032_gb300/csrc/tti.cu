@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(2 * TX * TY)
                      const __grid_constant__ CUtensorMap map_cint, const TtiArgs a, int zchunk,
                      int nzc) {
     using C = TtiCfg<R, TX, TY, D>;
+    if (__ldcg(a.err) & DEV_ERR_NONFINITE) return;  // stopped by the divergence watchdog
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Ring ring = ring_init<C::NSL, C::WARPS>(smem_raw, C::STAGE1, 0);
     const int tid = threadIdx.x, lane = tid & 31;
@@ -215,6 +216,7 @@ __global__ void __launch_bounds__(2 * TX * TY)
                      const __grid_constant__ CUtensorMap map_cint, const TtiArgs a, int zchunk,
                      int nzc) {
     using C = TtiCfg<R, TX, TY, D>;
+    if (__ldcg(a.err) & DEV_ERR_NONFINITE) return;  // stopped by the divergence watchdog
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Ring ring = ring_init<C::NSL, C::WARPS>(smem_raw, C::STAGE2, 4 * C::INT);
     float *xchg = ring.smem + C::NSL * C::STAGE2;  // [2 buffers][A | B][INT]
@@ -408,6 +410,7 @@ constexpr int kRecBX = 32, kRecBY = 8;
 
 template <int R, int K1, int K2>
 __global__ void __launch_bounds__(kRecBX *kRecBY) tti_recompute_kernel(const TtiArgs a) {
+    if (__ldcg(a.err) & DEV_ERR_NONFINITE) return;  // stopped by the divergence watchdog
     const WaveLayout &L = a.L;
     const int i = blockIdx.x * kRecBX + threadIdx.x;
     const int j = blockIdx.y * kRecBY + threadIdx.y;

@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(32 * TY)
                      const __grid_constant__ CUtensorMap map_cint, const TtiArgs a, int zchunk,
                      int nzc) {
     using C = TfCfg<R, D, TY>;
+    if (__ldcg(a.err) & DEV_ERR_NONFINITE) return;  // stopped by the divergence watchdog
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *smem = reinterpret_cast<float *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));

@@ -24,3 +24,11 @@ def require_cuda():
 def to_dev(torch, *arrays):
     return [None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
             for a in arrays]
+
+
+def max_abs_rel(a, b):
+    """max |a - b| / max |b|: a single wrong point in a large field moves the
+    relative L2 distance by little, but shows here."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-300))

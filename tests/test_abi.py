@@ -90,3 +90,73 @@ def test_missing_library_fails_loudly(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
     assert "raised" in r.stdout, r.stdout + r.stderr
     del _native
+
+
+def test_oversized_grids_are_rejected_before_any_device_work(lib):
+    """A padded volume of 2^32 points or more is rejected by the host checks
+    (the sparse tables index the volume in 32 bits), by every entry point
+    that sizes device memory from the grid -- including the allocation-free
+    call, whose scratch sizing would otherwise wrap -- with no CUDA call made
+    (this runs without a GPU)."""
+    import ctypes
+    from paper_1807_03032_gb300 import _native
+    huge = _native.grid_struct((1 << 21, 1 << 21, 1 << 21), (10.0, 10.0, 10.0),
+                               (0.0, 0.0, 0.0))
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: the grid check comes first
+    st = lib.acoustic_forward_noalloc(huge, 4, 1.0, 4, 1, fake, None, 0, None, None, 0, None,
+                                      None, None, None, None)
+    assert st == {v: k for k, v in _native.STATUS_NAMES.items()}["FD_ERR_ARG"], st
+    assert b"2^32" in lib.fd_last_error()
+    st = lib.acoustic_forward(huge, 4, 1.0, 4, 1, fake, None, 0, None, None, 0, None, None,
+                              None, None, None)
+    assert st == {v: k for k, v in _native.STATUS_NAMES.items()}["FD_ERR_ARG"], st
+    out = ctypes.c_void_p()
+    st = lib.fd_engine_create(huge, 8, 1.0, fake, None, 1, 1, 1, ctypes.byref(out))
+    assert st == {v: k for k, v in _native.STATUS_NAMES.items()}["FD_ERR_ARG"], st
+    nbytes = ctypes.c_int64()
+    st = lib.fd_engine_footprint(huge, 1, 1, 1, ctypes.byref(nbytes))
+    assert st == {v: k for k, v in _native.STATUS_NAMES.items()}["FD_ERR_ARG"], st
+    # a non-finite origin is rejected the same way
+    bad = _native.grid_struct((8, 8, 8), (10.0, 10.0, 10.0), (float("nan"), 0.0, 0.0))
+    st = lib.acoustic_forward_noalloc(bad, 4, 1.0, 4, 1, fake, None, 0, None, None, 0, None,
+                                      None, None, None, None)
+    assert st == {v: k for k, v in _native.STATUS_NAMES.items()}["FD_ERR_ARG"], st
+
+
+@pytest.mark.parametrize("so", [2, 4, 8, 12, 16])
+@pytest.mark.parametrize("spacing", [(20.0, 20.0, 20.0), (9.0, 11.0, 10.0), (5.0, 5.0, 12.5)])
+def test_device_laplacian_weights_sum_to_zero_exactly(so, spacing):
+    """The FP32 weights the acoustic kernels use: the Laplacian of a constant
+    is exactly zero (checked in exact rational arithmetic), as it is for the
+    closed-form weights (w_0 = -2 sum w_k, Listing fd-1 for so = 2); every
+    weight differs from the FP32 rounding of its exact value by at most one
+    ulp of the centre weight (the size of the residual that was moved), and
+    each axis keeps the second moment sum_k 2 k^2 w_k h^2 = 2 of a second
+    derivative to 1e-6 (a phase velocity error below 5e-7).  With
+    independently rounded weights the residual is a spurious mass term whose
+    phase error grows linearly in time (1.1e-4 relative L2 after the 1000 ms
+    acoustic workload at so = 12)."""
+    from fractions import Fraction
+    import numpy as np
+    from paper_1807_03032_gb300 import _native
+    from tests.fd_exact import second_derivative_weights
+    centre, w = _native.stencil_weights((8, 8, 8), spacing, so)
+    R = so // 2
+    total = Fraction(centre) + 2 * sum(Fraction(w[d][k]) for d in range(3) for k in range(1, 9))
+    assert total == 0
+    exact = second_derivative_weights(R)  # Fractions, index 0..R
+    want_c = float(sum(exact[0] / Fraction(h) ** 2 for h in spacing))
+    ulp_c = float(np.spacing(np.float32(abs(want_c))))
+    assert abs(centre - float(np.float32(want_c))) <= ulp_c
+    for d in range(3):
+        assert w[d][0] == 0.0
+        for k in range(1, 9):
+            want = float(exact[k] / Fraction(spacing[d]) ** 2) if k <= R else 0.0
+            got = w[d][k]
+            if k > R:
+                assert got == 0.0
+                continue
+            assert abs(got - float(np.float32(want))) <= ulp_c, (d, k, got, want)
+        moment = sum(2 * k * k * Fraction(w[d][k]) for k in range(1, R + 1)) * Fraction(
+            spacing[d]) ** 2
+        assert abs(float(moment) - 2.0) <= 1e-6 * 2.0

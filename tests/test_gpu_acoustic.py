@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import workloads
-from tests.gpu_util import TOL, rel_l2, require_cuda, to_dev
+from tests.gpu_util import TOL, max_abs_rel, rel_l2, require_cuda, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -261,6 +261,8 @@ def test_full_size_parity_first_steps():
                                              w.rec_xyz, damp=w.damp, u_init=u_init)
         assert rel_l2(uf, uref) <= TOL
         assert rel_l2(rec, rref) <= TOL
+        assert max_abs_rel(uf, uref) <= TOL
+        assert max_abs_rel(rec, rref) <= TOL
         del uf, uref
 
 

@@ -4,7 +4,7 @@ import pytest
 
 import oracle
 import workloads
-from tests.gpu_util import TOL, rel_l2, require_cuda, to_dev
+from tests.gpu_util import TOL, max_abs_rel, rel_l2, require_cuda, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -132,11 +132,13 @@ def test_full_size_tti_parity_first_steps():
     assert rel_l2(pf, pref) <= TOL
     assert rel_l2(rf, qref) <= TOL
     assert rel_l2(rec, rref) <= TOL
+    for got, ref in ((pf, pref), (rf, qref), (rec, rref)):
+        assert max_abs_rel(got, ref) <= TOL
 
 
-@pytest.mark.parametrize("so", [8, 16])
+@pytest.mark.parametrize("so", [8, 12, 16])
 def test_full_size_tti_two_pass_parity_first_steps(so):
-    """512^3 TTI with the two passes, as the benchmark runs so = 8 and 16
+    """512^3 TTI with the two passes, as the benchmark runs so = 8, 12 and 16
     (launch configuration included): two steps from smooth random p and r
     states with a source and the full receiver plane, against the oracle at
     every point."""
@@ -163,6 +165,8 @@ def test_full_size_tti_two_pass_parity_first_steps(so):
     assert rel_l2(pf, pref) <= TOL
     assert rel_l2(rf, qref) <= TOL
     assert rel_l2(rec, rref) <= TOL
+    for got, ref in ((pf, pref), (rf, qref), (rec, rref)):
+        assert max_abs_rel(got, ref) <= TOL
 
 
 def test_full_size_tti_full_run_is_linear_in_the_source():
