@@ -94,6 +94,8 @@ def _load():
                                             I, P, P, I, P, P, P, P, P, P]
             lib.ora_tti_forward_opts.argtypes = [G, I, I, I, I, D, I, I, P, P, P, P, P, P,
                                                  I, P, P, I, P, P, P, P, P, P]
+            lib.ora_tti_forward_storage.argtypes = [G, I, I, D, I, I, P, P, P, P, P, P,
+                                                    I, P, P, I, P, P, P, P, P, P, I]
             lib.ora_acoustic_adjoint.argtypes = [G, I, I, D, I, I, P, P, I, P, P, I, P, P]
             lib.ora_round_binary16.argtypes = [D]
             lib.ora_round_binary16.restype = D
@@ -104,7 +106,7 @@ def _load():
                          "ora_laplacian", "ora_first_derivative", "ora_acoustic_step",
                          "ora_interpolate", "ora_inject", "ora_acoustic_forward",
                          "ora_tti_operators", "ora_tti_forward", "ora_first_derivative_kind",
-                         "ora_tti_operators_kind", "ora_tti_forward_opts",
+                         "ora_tti_operators_kind", "ora_tti_forward_opts", "ora_tti_forward_storage",
                          "ora_acoustic_forward_storage"):
                 getattr(lib, name).restype = ctypes.c_int
             _lib = lib
@@ -294,9 +296,12 @@ def tti_operators(grid: Grid, so: int, theta, phi, q, periodic: bool = False,
 
 def tti_forward(grid: Grid, so: int, dt: float, nt: int, m, eps, delta, theta, phi, src_xyz,
                 src_wav, rec_xyz, damp=None, p_init=None, r_init=None, periodic: bool = False,
-                deriv: str = "centred", receiver: str = "p"):
+                deriv: str = "centred", receiver: str = "p", storage: str = "exact"):
     """Full TTI forward run.  Returns (rec, p_final, r_final) in FP64.
-    deriv: "centred" or "staggered"; receiver: "p" or "mean" ((p + r)/2)."""
+    deriv: "centred" or "staggered"; receiver: "p" or "mean" ((p + r)/2).
+    storage: "exact" (the FP64 model) or "f32" (a yardstick for FP32 storage:
+    a and s rounded to FP32, p and r rounded to FP32 after every step;
+    central derivatives and receivers on p only)."""
     m, eps, delta, theta, phi = (_f32(a) for a in (m, eps, delta, theta, phi))
     damp = _f32(damp)
     src_xyz, src_wav, rec_xyz = _f32(src_xyz), _f32(src_wav), _f32(rec_xyz)
@@ -307,7 +312,14 @@ def tti_forward(grid: Grid, so: int, dt: float, nt: int, m, eps, delta, theta, p
     pfin = np.zeros((nshots, 2) + m.shape)
     rfin = np.zeros((nshots, 2) + m.shape)
     lib = _load()
-    if deriv == "centred" and receiver == "p":
+    if storage != "exact":
+        if (deriv, receiver, storage) != ("centred", "p", "f32"):
+            raise ValueError("storage='f32' takes central derivatives and receivers on p")
+        st = lib.ora_tti_forward_storage(
+            ctypes.byref(grid), so, int(periodic), float(dt), int(nt), nshots, _ptr(m), _ptr(damp),
+            _ptr(eps), _ptr(delta), _ptr(theta), _ptr(phi), nsrc, _ptr(src_xyz), _ptr(src_wav),
+            nrec, _ptr(rec_xyz), _ptr(rec), _ptr(p_init), _ptr(r_init), _ptr(pfin), _ptr(rfin), 1)
+    elif deriv == "centred" and receiver == "p":
         st = lib.ora_tti_forward(ctypes.byref(grid), so, int(periodic), float(dt), int(nt),
                                  nshots, _ptr(m), _ptr(damp), _ptr(eps), _ptr(delta), _ptr(theta),
                                  _ptr(phi), nsrc, _ptr(src_xyz), _ptr(src_wav), nrec,

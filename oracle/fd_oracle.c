@@ -603,6 +603,17 @@ int ora_tti_operators(const ora_grid *g, int so, int periodic, const double *the
     return ora_tti_operators_kind(g, so, periodic, 0, theta, phi, q, hz, lq);
 }
 
+/* TTI coefficients a = 1 + 2 eps and s = sqrt(1 + 2 delta); with storage = 1
+ * rounded to FP32, as a device that stores them in FP32 uses them. */
+static double coef_a(double eps, int storage) {
+    const double a = 1.0 + 2.0 * eps;
+    return storage ? (double)(float)a : a;
+}
+static double coef_s(double delta, int storage) {
+    const double sv = sqrt(1.0 + 2.0 * delta);
+    return storage ? (double)(float)sv : sv;
+}
+
 /* TTI receivers: interp(p), or interp((p + r)/2) with receiver = 1 (tmp is
  * scratch of one field). */
 static void record(const ora_grid *g, int receiver, int nrec, const float *rxyz,
@@ -629,15 +640,22 @@ static void record(const ora_grid *g, int receiver, int nrec, const float *rxyz,
  * ora_tti_operators_kind.
  * Fields eps, delta, theta, phi are [nz][ny][nx].  p_init/r_init and
  * p_final/r_final are [nshots][2][nz][ny][nx] (levels n, n-1) or NULL.
+ *
+ * storage = 1 is a model of FP32 storage (not a reading of the paper; a
+ * yardstick for the device's rounding): the coefficients a = 1 + 2 eps and
+ * s = sqrt(1 + 2 delta) are rounded to FP32 once, and p^{n+1}, r^{n+1} are
+ * rounded to FP32 after every step (after the injection); all arithmetic
+ * stays FP64.  storage = 0 is the FP64 model.
  */
-int ora_tti_forward_opts(const ora_grid *g, int so, int periodic, int deriv, int receiver,
-                         double dt, int nt, int nshots, const float *m32, const float *damp32,
-                         const float *eps32, const float *delta32, const float *theta32,
-                         const float *phi32, int nsrc, const float *src_xyz,
-                         const float *src_wav, int nrec, const float *rec_xyz, double *rec_out,
-                         const float *p_init, const float *r_init, double *p_final,
-                         double *r_final) {
+static int tti_forward_impl(const ora_grid *g, int so, int periodic, int deriv, int receiver,
+                            double dt, int nt, int nshots, const float *m32, const float *damp32,
+                            const float *eps32, const float *delta32, const float *theta32,
+                            const float *phi32, int nsrc, const float *src_xyz,
+                            const float *src_wav, int nrec, const float *rec_xyz,
+                            double *rec_out, const float *p_init, const float *r_init,
+                            double *p_final, double *r_final, int storage) {
     if (radius_of(so) < 0 || nt < 1 || nshots < 1 || nsrc < 0 || nrec < 0) return ORA_ERR_ARG;
+    if (storage < 0 || storage > 1) return ORA_ERR_ARG;
     if (deriv < 0 || deriv > 1 || receiver < 0 || receiver > 1) return ORA_ERR_ARG;
     const size_t N = npts(g);
     for (int s = 0; s < nshots; ++s) {
@@ -678,16 +696,24 @@ int ora_tti_forward_opts(const ora_grid *g, int so, int periodic, int deriv, int
             /* p equation: rhs = (1+2eps)(Lp - Hz p) + sqrt(1+2delta) Hz r */
 #pragma omp parallel for schedule(static)
             for (size_t i = 0; i < N; ++i)
-                rhs[i] = (1.0 + 2.0 * eps[i]) * (lp[i] - hzp[i]) + sqrt(1.0 + 2.0 * del[i]) * hzr[i];
+                rhs[i] = coef_a(eps[i], storage) * (lp[i] - hzp[i]) +
+                         coef_s(del[i], storage) * hzr[i];
             leapfrog(g, dt, m, damp, rhs, p, pm, pn);
             /* r equation: rhs = sqrt(1+2delta)(Lp - Hz p) + Hz r */
 #pragma omp parallel for schedule(static)
             for (size_t i = 0; i < N; ++i)
-                rhs[i] = sqrt(1.0 + 2.0 * del[i]) * (lp[i] - hzp[i]) + hzr[i];
+                rhs[i] = coef_s(del[i], storage) * (lp[i] - hzp[i]) + hzr[i];
             leapfrog(g, dt, m, damp, rhs, r, rm, rn);
             for (int k = 0; k < nsrc; ++k) q[k] = (double)src_wav[((size_t)s * nt + n) * nsrc + k];
             ora_inject(g, nsrc, sxyz, q, scale, pn);
             ora_inject(g, nsrc, sxyz, q, scale, rn);
+            if (storage) {
+#pragma omp parallel for schedule(static)
+                for (size_t i = 0; i < N; ++i) {
+                    pn[i] = (double)(float)pn[i];
+                    rn[i] = (double)(float)rn[i];
+                }
+            }
             if (rec) record(g, receiver, nrec, rxyz, p, r, rhs, rec + (size_t)n * nrec);
             double *t = pm;
             pm = p;
@@ -719,6 +745,31 @@ done:
     free(q);
     for (int b = 0; b < 10; ++b) free(bufs[b]);
     return st;
+}
+
+int ora_tti_forward_opts(const ora_grid *g, int so, int periodic, int deriv, int receiver,
+                         double dt, int nt, int nshots, const float *m32, const float *damp32,
+                         const float *eps32, const float *delta32, const float *theta32,
+                         const float *phi32, int nsrc, const float *src_xyz,
+                         const float *src_wav, int nrec, const float *rec_xyz, double *rec_out,
+                         const float *p_init, const float *r_init, double *p_final,
+                         double *r_final) {
+    return tti_forward_impl(g, so, periodic, deriv, receiver, dt, nt, nshots, m32, damp32, eps32,
+                            delta32, theta32, phi32, nsrc, src_xyz, src_wav, nrec, rec_xyz,
+                            rec_out, p_init, r_init, p_final, r_final, 0);
+}
+
+/* The TTI forward model (central derivatives, receivers on p) with the FP32
+ * storage model of tti_forward_impl (storage = 1) or without it (0). */
+int ora_tti_forward_storage(const ora_grid *g, int so, int periodic, double dt, int nt,
+                            int nshots, const float *m32, const float *damp32, const float *eps32,
+                            const float *delta32, const float *theta32, const float *phi32,
+                            int nsrc, const float *src_xyz, const float *src_wav, int nrec,
+                            const float *rec_xyz, double *rec_out, const float *p_init,
+                            const float *r_init, double *p_final, double *r_final, int storage) {
+    return tti_forward_impl(g, so, periodic, 0, 0, dt, nt, nshots, m32, damp32, eps32, delta32,
+                            theta32, phi32, nsrc, src_xyz, src_wav, nrec, rec_xyz, rec_out, p_init,
+                            r_init, p_final, r_final, storage);
 }
 
 int ora_tti_forward(const ora_grid *g, int so, int periodic, double dt, int nt, int nshots,

@@ -10,6 +10,11 @@ binary16 value, a run without steps returns the rounded initial state, the
 first injection from rest lands exactly where hand arithmetic in numpy's
 float16 puts it, and the accumulated storage error stays within the size that
 per-step rounding allows.
+
+The TTI FP32 storage model (the yardstick for the device's final TTI fields
+over long runs) is pinned the same way: it stores FP32 values only, keeps the
+initial state, makes one step equal to the rounded FP64 step where the
+coefficients are FP32 values, and reduces to the FP64 model without rounding.
 """
 import numpy as np
 import pytest
@@ -165,3 +170,69 @@ def test_f16_step_is_the_stored_step_with_binary16_coefficient():
     np.testing.assert_array_equal(uz[0, 0], as_f16(uc[0, 0].astype(np.float32)))
     np.testing.assert_array_equal(uz[0, 1], uc[0, 1])
     assert rel(uf[0, 0], uz[0, 0]) > 0  # the source shows with a nonzero wavelet
+
+
+# ---------------------------------------------------------------- TTI FP32 storage model
+
+def _tti_case(n=16, nt=3, seed=4, eps_zero=False):
+    shape = (n, n, n)
+    h = (10.0, 10.0, 10.0)
+    rng = np.random.default_rng(seed)
+    eps = np.zeros(shape) if eps_zero else rng.uniform(0.0, 0.3, shape)
+    delta = np.zeros(shape) if eps_zero else np.minimum(rng.uniform(0.0, 0.2, shape), eps)
+    theta = rng.uniform(0.0, np.pi / 4, shape)
+    phi = rng.uniform(0.0, np.pi / 4, shape)
+    m = workloads.slowness_squared(rng.uniform(1.5, 2.5, shape))
+    dt = 0.5 * workloads.cfl_dt(h, 2.5, eps_max=0.3)
+    c = (n / 2 - 0.3) * h[0]
+    src = np.array([[[c, c, c]]], np.float32)
+    rec = np.array([[[c, c - 10.0, c + 15.0], [20.0, 30.0, 40.0]]], np.float32)
+    wav = rng.standard_normal((1, nt, 1)).astype(np.float32)
+    p0 = (1e-2 * rng.standard_normal((1, 2) + shape)).astype(np.float32)
+    r0 = (1e-2 * rng.standard_normal((1, 2) + shape)).astype(np.float32)
+    f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    og = oracle.make_grid(shape, h)
+    args = (og, 8, dt, nt, m, f32(eps), f32(delta), f32(theta), f32(phi), src, wav, rec)
+    return args, p0, r0
+
+
+def test_tti_f32_storage_stores_fp32_values_and_keeps_the_initial_state():
+    """Every value the FP32 storage model stores is an FP32 value, and a run
+    without steps returns the initial state (already FP32) unchanged."""
+    args, p0, r0 = _tti_case(nt=4)
+    _, p, r = oracle.tti_forward(*args, p_init=p0, r_init=r0, storage="f32")
+    for f in (p, r):
+        np.testing.assert_array_equal(f, f.astype(np.float32).astype(np.float64))
+    args1 = args[:3] + (1,) + args[4:10] + (np.zeros((1, 1, 1), np.float32),) + args[11:]
+    _, p1, r1 = oracle.tti_forward(*args1, p_init=p0, r_init=r0, storage="f32")
+    np.testing.assert_array_equal(p1, p0)
+    np.testing.assert_array_equal(r1, r0)
+
+
+def test_tti_f32_storage_one_step_is_the_rounded_exact_step():
+    """With eps = delta = 0 the coefficients a = s = 1 are FP32 values, so one
+    step of the storage model is the FP64 step (injection included) rounded
+    once to FP32, and the level below it is the initial state."""
+    args, p0, r0 = _tti_case(nt=2, eps_zero=True)
+    _, pe, re_ = oracle.tti_forward(*args, p_init=p0, r_init=r0)
+    _, pm, rm = oracle.tti_forward(*args, p_init=p0, r_init=r0, storage="f32")
+    np.testing.assert_array_equal(pm[0, 0], pe[0, 0].astype(np.float32).astype(np.float64))
+    np.testing.assert_array_equal(rm[0, 0], re_[0, 0].astype(np.float32).astype(np.float64))
+    np.testing.assert_array_equal(pm[0, 1], p0[0, 0])
+    assert np.any(pm[0, 0] != pe[0, 0])  # the rounding did something
+
+
+def test_tti_f32_storage_rounds_the_coefficients():
+    """With eps and delta whose a = 1 + 2 eps and s = sqrt(1 + 2 delta) are
+    not FP32 values, one step of the storage model differs from the rounded
+    exact step (the coefficients are rounded before they are used), but by no
+    more than FP32 rounding of the coefficients can explain (relative 1e-6),
+    and the model without rounding is the FP64 model bit for bit."""
+    args, p0, r0 = _tti_case(nt=2)
+    _, pe, _ = oracle.tti_forward(*args, p_init=p0, r_init=r0)
+    _, pm, _ = oracle.tti_forward(*args, p_init=p0, r_init=r0, storage="f32")
+    rounded = pe[0, 0].astype(np.float32).astype(np.float64)
+    assert np.any(pm[0, 0] != rounded)
+    assert rel(pm[0, 0], pe[0, 0]) < 1e-6
+    _, px, _ = oracle.tti_forward(*args, p_init=p0, r_init=r0, storage="exact")
+    np.testing.assert_array_equal(px, pe)
