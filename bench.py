@@ -706,6 +706,40 @@ def run_serving(args, fd, dev, gpts_so8):
             "latency_is": "job arrival to delivery of its last shot's traces (device)"}
 
 
+def run_batched_probe(args):
+    """Diagnostic (not the benchmark line): one acoustic forward of S shots
+    sharing a two-layer 256^3 model (so 8, nt 4, one source and one receiver
+    per shot), then three 12-step calls timed with the library's per-launch
+    events; prints the stencil kernel's rate over all shots.  Used to capture
+    the DRAM bytes per shot-point of a shot-batched launch with ncu."""
+    import torch
+    import paper_1807_03032_gb300 as fd
+    from paper_1807_03032_gb300 import _native
+    S, n, h = args.batched_probe, args.batched_n, 20.0
+    shape = (n, n, n)
+    m = workloads.slowness_squared(workloads.two_layer_velocity(shape, 1.5, 2.5))
+    damp = workloads.damping_profile(shape, 20, (h, h, h), 2.5)
+    dt = workloads.cfl_dt((h, h, h), 2.5)
+    c = (n / 2 - 0.5) * h
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    g = fd.Grid(shape, (h, h, h))
+    mt, dd = T(m), T(damp)
+    sx = T(np.tile(np.array([c, c, 30 * h]), (S, 1, 1)))
+    rx = T(np.tile(np.array([[c, c, 25 * h]]), (S, 1, 1)))
+    for nt in (4, 12, 12, 12):
+        if nt == 12 and not _native.stats_get("acoustic_step")[1]:
+            _native.stats_reset()
+            _native.stats_enable(True)
+        sw = T(np.tile(workloads.ricker(nt, dt)[None, :, None], (S, 1, 1)))
+        fd.acoustic_forward(g, 8, dt, nt, mt, sx, sw, rx, damp=dd, return_final=False)
+    torch.cuda.synchronize()
+    ms, k, pts = _native.stats_get("acoustic_step")
+    _native.stats_enable(False)
+    print(json.dumps({"probe": "batched shots", "shots": S, "grid": n, "so": 8,
+                      "kernel_us": round(ms / k * 1e3, 1),
+                      "kernel_gpts_all_shots": round(pts / (ms / k * 1e-3) / 1e9, 1)}), flush=True)
+
+
 def cpu_baseline(w, so_list):
     """The FP64 oracle, as it stands, on the host cores: one time step of the
     512^3 workload at each space order (a bounded sample of the workload)."""
@@ -814,9 +848,14 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--fwi-n", type=int, default=256)
     ap.add_argument("--fwi-nt", type=int, default=2000)
+    ap.add_argument("--batched-probe", type=int, default=0, metavar="S",
+                    help="diagnostic only: one forward of S shots on a 256^3 so-8 model")
+    ap.add_argument("--batched-n", type=int, default=256)
     args = ap.parse_args()
     args.so = tuple(args.so)
-    if args.impl == "reference":
+    if args.batched_probe:
+        run_batched_probe(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -88,6 +88,8 @@ def _load():
             lib.ora_interpolate.argtypes = [G, I, P, P, P]
             lib.ora_inject.argtypes = [G, I, P, P, P, P]
             lib.ora_acoustic_forward.argtypes = [G, I, I, D, I, I, P, P, I, P, P, I, P, P, P, P]
+            lib.ora_acoustic_forward_field.argtypes = [G, I, I, D, I, I, P, P, I, P, P, I, P, P,
+                                                       P, P]
             lib.ora_tti_operators.argtypes = [G, I, I, P, P, P, P, P]
             lib.ora_tti_operators_kind.argtypes = [G, I, I, I, P, P, P, P, P]
             lib.ora_tti_forward.argtypes = [G, I, I, D, I, I, P, P, P, P, P, P,
@@ -105,6 +107,7 @@ def _load():
             for name in ("ora_acoustic_adjoint", "ora_acoustic_gradient",
                          "ora_laplacian", "ora_first_derivative", "ora_acoustic_step",
                          "ora_interpolate", "ora_inject", "ora_acoustic_forward",
+                         "ora_acoustic_forward_field",
                          "ora_tti_operators", "ora_tti_forward", "ora_first_derivative_kind",
                          "ora_tti_operators_kind", "ora_tti_forward_opts", "ora_tti_forward_storage",
                          "ora_acoustic_forward_storage"):
@@ -211,12 +214,13 @@ def inject(grid: Grid, xyz, q, scale, u):
 
 
 def acoustic_forward(grid: Grid, so: int, dt: float, nt: int, m, src_xyz, src_wav, rec_xyz,
-                     damp=None, u_init=None, periodic: bool = False):
+                     damp=None, u_init=None, periodic: bool = False, damp_layout: str = "axes"):
     """Full acoustic forward run.
 
     src_xyz [nshots][nsrc][3], src_wav [nshots][nt][nsrc], rec_xyz [nshots][nrec][3],
-    u_init [nshots][2][nz][ny][nx] or None.  Returns (rec [nshots][nt][nrec],
-    u_final [nshots][2][nz][ny][nx]) in FP64.
+    u_init [nshots][2][nz][ny][nx] or None; damp per-axis profiles [nx+ny+nz]
+    (damp_layout "axes") or a 3-D field [nz][ny][nx] ("field").  Returns
+    (rec [nshots][nt][nrec], u_final [nshots][2][nz][ny][nx]) in FP64.
     """
     m = _f32(m)
     damp = _f32(damp)
@@ -226,10 +230,11 @@ def acoustic_forward(grid: Grid, so: int, dt: float, nt: int, m, src_xyz, src_wa
     nrec = rec_xyz.shape[1]
     rec = np.zeros((nshots, nt, nrec))
     ufin = np.zeros((nshots, 2) + m.shape)
-    st = _load().ora_acoustic_forward(ctypes.byref(grid), so, int(periodic), float(dt), int(nt),
-                                      nshots, _ptr(m), _ptr(damp), nsrc, _ptr(src_xyz),
-                                      _ptr(src_wav), nrec, _ptr(rec_xyz), _ptr(rec),
-                                      _ptr(u_init), _ptr(ufin))
+    fn = {"axes": _load().ora_acoustic_forward,
+          "field": _load().ora_acoustic_forward_field}[damp_layout]
+    st = fn(ctypes.byref(grid), so, int(periodic), float(dt), int(nt), nshots, _ptr(m),
+            _ptr(damp), nsrc, _ptr(src_xyz), _ptr(src_wav), nrec, _ptr(rec_xyz), _ptr(rec),
+            _ptr(u_init), _ptr(ufin))
     _check(st, "acoustic_forward")
     return rec, ufin
 

@@ -198,10 +198,25 @@ int ora_first_derivative(const ora_grid *g, int so, int periodic, int axis, cons
     return ora_first_derivative_kind(g, so, periodic, axis, 0, f, out);
 }
 
-/* damp(i,j,k) from the per-axis 1-D profiles (NULL = no damping). */
+/* damp(i,j,k) from the damping field, one FP64 value per grid point (NULL =
+ * no damping).  The callers build the field from the API's input: either the
+ * per-axis 1-D profiles, damp(i,j,k) = d_x[i] + d_y[j] + d_z[k], or a 3-D
+ * field given point by point (section "Test case setup" names only an
+ * absorbing mask; both readings are served). */
 static double damp_at(const ora_grid *g, const double *damp, int i, int j, int k) {
     if (!damp) return 0.0;
-    return damp[i] + damp[g->nx + j] + damp[g->nx + g->ny + k];
+    return damp[lin(g, i, j, k)];
+}
+
+/* The FP64 damping field of per-axis FP64 profiles [nx | ny | nz]. */
+static double *damping_from_axes(const ora_grid *g, const double *axes) {
+    double *d = (double *)malloc(npts(g) * sizeof(double));
+    if (!d) return NULL;
+    for (int k = 0; k < g->nz; ++k)
+        for (int j = 0; j < g->ny; ++j)
+            for (int i = 0; i < g->nx; ++i)
+                d[lin(g, i, j, k)] = axes[i] + axes[g->nx + j] + axes[g->nx + g->ny + k];
+    return d;
 }
 
 /* Leapfrog update of the damped acoustic equation at every grid point, from
@@ -222,14 +237,27 @@ static void leapfrog(const ora_grid *g, double dt, const double *m, const double
             }
 }
 
-/* One acoustic time step u^{n+1} from (u^n, u^{n-1}). */
-int ora_acoustic_step(const ora_grid *g, int so, int periodic, double dt, const double *m,
-                      const double *damp, const double *u, const double *uprev, double *unext) {
+/* One acoustic time step u^{n+1} from (u^n, u^{n-1}); damp is a damping
+ * field (one value per point) or NULL. */
+static int acoustic_step_field(const ora_grid *g, int so, int periodic, double dt,
+                               const double *m, const double *damp, const double *u,
+                               const double *uprev, double *unext) {
     double *lap = (double *)malloc(npts(g) * sizeof(double));
     if (!lap) return ORA_ERR_OOM;
     int st = ora_laplacian(g, so, periodic, u, lap);
     if (st == ORA_OK) leapfrog(g, dt, m, damp, lap, u, uprev, unext);
     free(lap);
+    return st;
+}
+
+/* One acoustic time step u^{n+1} from (u^n, u^{n-1}); damp holds the per-axis
+ * profiles [nx | ny | nz] or is NULL. */
+int ora_acoustic_step(const ora_grid *g, int so, int periodic, double dt, const double *m,
+                      const double *damp, const double *u, const double *uprev, double *unext) {
+    double *field = damp ? damping_from_axes(g, damp) : NULL;
+    if (damp && !field) return ORA_ERR_OOM;
+    int st = acoustic_step_field(g, so, periodic, dt, m, field, u, uprev, unext);
+    free(field);
     return st;
 }
 
@@ -293,6 +321,19 @@ static double *widen(const float *src, size_t n) {
     return d;
 }
 
+/* The FP64 damping field of the API's FP32 damping input (NULL: none):
+ * per-axis profiles [nx | ny | nz] (dense = 0) or one value per point
+ * [nz][ny][nx] (dense = 1). */
+static double *damping_field(const ora_grid *g, const float *damp32, int dense) {
+    if (!damp32) return NULL;
+    if (dense) return widen(damp32, npts(g));
+    double *axes = widen(damp32, (size_t)g->nx + g->ny + g->nz);
+    if (!axes) return NULL;
+    double *d = damping_from_axes(g, axes);
+    free(axes);
+    return d;
+}
+
 static int check_sparse(const ora_grid *g, int npt, const float *xyz) {
     for (int p = 0; p < npt; ++p) {
         size_t idx[8];
@@ -322,14 +363,17 @@ static void injection_scale(const ora_grid *g, double dt, const double *m, const
  *   rec[nt-1] = interp(u^{nt-1});  u_final = (u^{nt-1}, u^{nt-2}).
  * The per-step order is the paper's schedule of a time iteration: stencil
  * update, then the sparse injection into the t+1 field.
- * Array shapes: m [nz][ny][nx]; damp [nx+ny+nz] or NULL; src_xyz
- * [nshots][nsrc][3]; src_wav [nshots][nt][nsrc]; rec_xyz [nshots][nrec][3];
- * rec_out [nshots][nt][nrec]; u_init/u_final [nshots][2][nz][ny][nx] or NULL.
+ * Array shapes: m [nz][ny][nx]; damp [nx+ny+nz] (per-axis profiles,
+ * damp_dense = 0) or [nz][ny][nx] (a 3-D field, damp_dense = 1) or NULL;
+ * src_xyz [nshots][nsrc][3]; src_wav [nshots][nt][nsrc]; rec_xyz
+ * [nshots][nrec][3]; rec_out [nshots][nt][nrec]; u_init/u_final
+ * [nshots][2][nz][ny][nx] or NULL.
  */
-int ora_acoustic_forward(const ora_grid *g, int so, int periodic, double dt, int nt, int nshots,
-                         const float *m32, const float *damp32, int nsrc, const float *src_xyz,
-                         const float *src_wav, int nrec, const float *rec_xyz, double *rec_out,
-                         const float *u_init, double *u_final) {
+static int acoustic_forward_impl(const ora_grid *g, int so, int periodic, double dt, int nt,
+                                 int nshots, const float *m32, const float *damp32,
+                                 int damp_dense, int nsrc, const float *src_xyz,
+                                 const float *src_wav, int nrec, const float *rec_xyz,
+                                 double *rec_out, const float *u_init, double *u_final) {
     if (radius_of(so) < 0 || nt < 1 || nshots < 1 || nsrc < 0 || nrec < 0) return ORA_ERR_ARG;
     const size_t N = npts(g);
     for (int s = 0; s < nshots; ++s) {
@@ -337,7 +381,7 @@ int ora_acoustic_forward(const ora_grid *g, int so, int periodic, double dt, int
         if (check_sparse(g, nrec, rec_xyz + (size_t)s * nrec * 3)) return ORA_ERR_COORD;
     }
     double *m = widen(m32, N);
-    double *damp = damp32 ? widen(damp32, (size_t)g->nx + g->ny + g->nz) : NULL;
+    double *damp = damping_field(g, damp32, damp_dense);
     double *scale = (double *)malloc(N * sizeof(double));
     double *u = (double *)malloc(N * sizeof(double));
     double *um = (double *)malloc(N * sizeof(double));
@@ -358,7 +402,7 @@ int ora_acoustic_forward(const ora_grid *g, int so, int periodic, double dt, int
             um[p] = u_init ? (double)u_init[((size_t)s * 2 + 1) * N + p] : 0.0;
         }
         for (int n = 0; n + 1 < nt; ++n) {
-            st = ora_acoustic_step(g, so, periodic, dt, m, damp, u, um, un);
+            st = acoustic_step_field(g, so, periodic, dt, m, damp, u, um, un);
             if (st) goto done;
             for (int p = 0; p < nsrc; ++p) q[p] = (double)src_wav[((size_t)s * nt + n) * nsrc + p];
             ora_inject(g, nsrc, sxyz, q, scale, un);
@@ -383,6 +427,26 @@ done:
     free(un);
     free(q);
     return st;
+}
+
+int ora_acoustic_forward(const ora_grid *g, int so, int periodic, double dt, int nt, int nshots,
+                         const float *m32, const float *damp32, int nsrc, const float *src_xyz,
+                         const float *src_wav, int nrec, const float *rec_xyz, double *rec_out,
+                         const float *u_init, double *u_final) {
+    return acoustic_forward_impl(g, so, periodic, dt, nt, nshots, m32, damp32, 0, nsrc, src_xyz,
+                                 src_wav, nrec, rec_xyz, rec_out, u_init, u_final);
+}
+
+/* The acoustic forward model with the damping given as a 3-D field
+ * damp[nz][ny][nx] (one value per point, NULL = none) instead of per-axis
+ * profiles. */
+int ora_acoustic_forward_field(const ora_grid *g, int so, int periodic, double dt, int nt,
+                               int nshots, const float *m32, const float *damp32, int nsrc,
+                               const float *src_xyz, const float *src_wav, int nrec,
+                               const float *rec_xyz, double *rec_out, const float *u_init,
+                               double *u_final) {
+    return acoustic_forward_impl(g, so, periodic, dt, nt, nshots, m32, damp32, 1, nsrc, src_xyz,
+                                 src_wav, nrec, rec_xyz, rec_out, u_init, u_final);
 }
 
 /*
@@ -455,7 +519,7 @@ int ora_acoustic_forward_storage(const ora_grid *g, int so, int periodic, double
         if (check_sparse(g, nrec, rec_xyz + (size_t)s * nrec * 3)) return ORA_ERR_COORD;
     }
     double *m = widen(m32, N);
-    double *damp = damp32 ? widen(damp32, (size_t)g->nx + g->ny + g->nz) : NULL;
+    double *damp = damping_field(g, damp32, 0);
     double *b = (double *)malloc(N * sizeof(double));
     double *lap = (double *)malloc(N * sizeof(double));
     double *u = (double *)malloc(N * sizeof(double));
@@ -665,7 +729,7 @@ static int tti_forward_impl(const ora_grid *g, int so, int periodic, int deriv, 
     int st = ORA_OK;
     double *m = widen(m32, N), *eps = widen(eps32, N), *del = widen(delta32, N);
     double *th = widen(theta32, N), *ph = widen(phi32, N);
-    double *damp = damp32 ? widen(damp32, (size_t)g->nx + g->ny + g->nz) : NULL;
+    double *damp = damping_field(g, damp32, 0);
     double *scale = (double *)malloc(N * sizeof(double));
     double *bufs[10];
     for (int b = 0; b < 10; ++b) bufs[b] = (double *)malloc(N * sizeof(double));
@@ -842,7 +906,7 @@ int ora_acoustic_adjoint(const ora_grid *g, int so, int periodic, double dt, int
     }
     int st = ORA_OK;
     double *m = widen(m32, N);
-    double *damp = damp32 ? widen(damp32, (size_t)g->nx + g->ny + g->nz) : NULL;
+    double *damp = damping_field(g, damp32, 0);
     double *l0 = (double *)calloc(N, sizeof(double)), *l1 = (double *)calloc(N, sizeof(double));
     double *l2 = (double *)calloc(N, sizeof(double)), *tmp = (double *)malloc(N * sizeof(double));
     double *ltmp = (double *)malloc(N * sizeof(double)), *ones = (double *)malloc(N * sizeof(double));
@@ -914,7 +978,7 @@ int ora_acoustic_gradient(const ora_grid *g, int so, double dt, int nt, int nsho
     }
     int st = ORA_OK;
     double *m = widen(m32, N);
-    double *damp = damp32 ? widen(damp32, (size_t)g->nx + g->ny + g->nz) : NULL;
+    double *damp = damping_field(g, damp32, 0);
     double *hist = (double *)malloc((size_t)(nt + 1) * N * sizeof(double)); /* u^{-1..nt-1} */
     double *scale = (double *)malloc(N * sizeof(double));
     double *q = (double *)malloc(((size_t)nsrc + 1) * sizeof(double));
@@ -939,7 +1003,7 @@ int ora_acoustic_gradient(const ora_grid *g, int so, double dt, int nt, int nsho
         memset(U(-1), 0, N * sizeof(double));
         memset(U(0), 0, N * sizeof(double));
         for (int n = 0; n + 1 < nt; ++n) {
-            st = ora_acoustic_step(g, so, 0, dt, m, damp, U(n), U(n - 1), U(n + 1));
+            st = acoustic_step_field(g, so, 0, dt, m, damp, U(n), U(n - 1), U(n + 1));
             if (st) goto done;
             for (int k = 0; k < nsrc; ++k) q[k] = (double)src_wav[((size_t)s * nt + n) * nsrc + k];
             ora_inject(g, nsrc, sxyz, q, scale, U(n + 1));
