@@ -102,7 +102,7 @@ fd_status acoustic_forward(const fd_grid *grid, int so, double dt, int nt, int n
 
 /*
  * acoustic_forward_opts -- acoustic_forward with a choice of storage
- * precision.  The paper names mixed-precision arithmetic and on-the-fly data
+ * precision and of the damping input's layout.  The paper names mixed-precision arithmetic and on-the-fly data
  * compression as further performance work (section "Further work"); the step
  * is memory bound, so halving the stored bytes per point is the lever.
  *
@@ -124,13 +124,28 @@ fd_status acoustic_forward(const fd_grid *grid, int so, double dt, int nt, int n
  *                  FD_ERR_DIVERGED).  Radii with a binary16 kernel: so = 2..16
  *                  (FD_ERR_UNIMPL otherwise); time tiling is not combined
  *                  with it.
- *   opts           NULL selects FD_STORAGE_F32.  Out-of-range values return
- *                  FD_ERR_ARG.
+ *   opts->damp_layout
+ *                  FD_DAMP_AXES: damp holds the per-axis profiles
+ *                  [nx + ny + nz] of acoustic_forward (damp(i,j,k) = d_x[i] +
+ *                  d_y[j] + d_z[k]; the stencil forms the damping from them,
+ *                  16 bytes per point and step).
+ *                  FD_DAMP_FIELD: damp is a 3-D field [nz][ny][nx] (any
+ *                  finite non-negative absorbing mask, separable or not; the
+ *                  paper's section "Test case setup" names only "absorbing
+ *                  boundaries with a 10 point mask").  The stencil kernel
+ *                  then reads one more coefficient per point, zeta = damp b
+ *                  / dt (20 bytes per point and step).  FP32 storage only
+ *                  (FD_ERR_ARG with FD_STORAGE_F16); time tiling is not
+ *                  combined with it.  NULL damp: no damping, either layout.
+ *   opts           NULL selects FD_STORAGE_F32 and FD_DAMP_AXES.
+ *                  Out-of-range values return FD_ERR_ARG.
  * Other arguments, ownership and errors as for acoustic_forward.
  */
 enum { FD_STORAGE_F32 = 0, FD_STORAGE_F16 = 1 };
+enum { FD_DAMP_AXES = 0, FD_DAMP_FIELD = 1 };
 typedef struct {
     int32_t storage;
+    int32_t damp_layout;
 } fd_acoustic_options;
 
 fd_status acoustic_forward_opts(const fd_grid *grid, int so, double dt, int nt, int nshots,

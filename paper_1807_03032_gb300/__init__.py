@@ -88,10 +88,13 @@ def _as_grid(grid):
 
 
 def acoustic_forward(grid, so, dt, nt, m, src_xyz, src_wav, rec_xyz, damp=None, u_init=None,
-                     rec_out=None, u_final=None, return_final=True, stream=None, storage="f32"):
+                     rec_out=None, u_final=None, return_final=True, stream=None, storage="f32",
+                     damp_layout="axes"):
     """Isotropic acoustic forward model (C ABI ``acoustic_forward``).
 
-    m [nz][ny][nx]; damp [nx+ny+nz] per-axis profiles or None;
+    m [nz][ny][nx]; damp [nx+ny+nz] per-axis profiles (damp_layout "axes")
+    or a 3-D field [nz][ny][nx] ("field": C ABI ``acoustic_forward_opts``
+    with FD_DAMP_FIELD), or None;
     src_xyz [nshots][nsrc][3]; src_wav [nshots][nt][nsrc]; rec_xyz [nshots][nrec][3];
     u_init [nshots][2][nz][ny][nx] (u^0, u^-1) or None.
     storage: "f32" or "f16" (wavefields and b held in IEEE binary16 on the
@@ -116,10 +119,11 @@ def acoustic_forward(grid, so, dt, nt, m, src_xyz, src_wav, rec_xyz, damp=None, 
             _ptr(rec_xyz, "rec_xyz"), _ptr(rec_out, "rec_out"), _ptr(u_init, "u_init"),
             _ptr(u_final, "u_final"))
     stream_ptr = _stream_for(m, rec_out, stream=stream)
-    if storage == "f32":
+    if storage == "f32" and damp_layout == "axes":
         st = lib.acoustic_forward(*args, stream_ptr)
     else:
-        opts = _native.FdAcousticOptions(_native.STORAGE[storage])
+        opts = _native.FdAcousticOptions(_native.STORAGE[storage],
+                                         _native.DAMP_LAYOUT[damp_layout])
         st = lib.acoustic_forward_opts(*args, ctypes.byref(opts), stream_ptr)
     _native.check(st)
     return rec_out, u_final

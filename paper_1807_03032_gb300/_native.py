@@ -51,10 +51,11 @@ class FdTtiOptions(ctypes.Structure):
 class FdAcousticOptions(ctypes.Structure):
     """Mirror of fd_acoustic_options."""
 
-    _fields_ = [("storage", ctypes.c_int32)]
+    _fields_ = [("storage", ctypes.c_int32), ("damp_layout", ctypes.c_int32)]
 
 
 STORAGE = {"f32": 0, "f16": 1}
+DAMP_LAYOUT = {"axes": 0, "field": 1}
 TTI_DERIV = {"centred": 0, "staggered": 1}
 TTI_RECEIVER = {"p": 0, "mean": 1}
 TTI_SCHEME = {"auto": -1, "two_pass": 0, "recompute": 1, "fused": 2}

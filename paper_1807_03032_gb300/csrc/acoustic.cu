@@ -38,7 +38,11 @@ namespace fdsweep {
 namespace {
 using namespace f32x2;
 
-template <int R, int TX, int TY, int VY, int D>
+// DF: the damping is a 3-D field; the stage then also carries the interior
+// tile of the per-point coefficient zeta = damp b / dt (stored after b as a
+// second field of the coefficient tensor) instead of forming zeta from the
+// per-axis profiles: 20 instead of 16 bytes per point.
+template <int R, int TX, int TY, int VY, int D, bool DF = false>
 struct AcCfg {
     static constexpr int BX = 4 * TX;
     static constexpr int BY = VY * TY;
@@ -48,7 +52,8 @@ struct AcCfg {
     static constexpr int NSL = D + 1;           // ring slots
     static constexpr int HALO = (PW * PH + 31) / 32 * 32;
     static constexpr int INT = BX * BY;         // interior tile (multiple of 32)
-    static constexpr int STAGE = HALO + 3 * INT;  // [halo u^n][u^n][u^{n-1}][b]
+    static constexpr int NINT = DF ? 4 : 3;     // interior tiles per stage
+    static constexpr int STAGE = HALO + NINT * INT;  // [halo u^n][u^n][u^{n-1}][b][zeta]
     static constexpr uint32_t HALO_BYTES = PW * PH * 4;
     static constexpr uint32_t INT_BYTES = INT * 4;
     static constexpr int THREADS = TX * TY;
@@ -103,14 +108,14 @@ __device__ __noinline__ void inject_column(const AcousticStepArgs *a, const Acou
 // U: unroll factor of the plane loop.  The pending-output registers shift by
 // one plane per iteration; unrolling by U turns U - 1 of every U shifts into
 // register renaming instead of moves (U = 2R removes them all).
-template <int R, int TX, int TY, int VY, int D, int U>
+template <int R, int TX, int TY, int VY, int D, int U, bool DF>
 __global__ void __launch_bounds__(TX *TY)
     acoustic_step_kernel(const __grid_constant__ CUtensorMap map_halo,
                          const __grid_constant__ CUtensorMap map_int,
                          const __grid_constant__ CUtensorMap map_b,
                          const __grid_constant__ AcousticStepArgs a,
                          const __grid_constant__ AcousticInject inj, int zchunk, int nzc) {
-    using C = AcCfg<R, TX, TY, VY, D>;
+    using C = AcCfg<R, TX, TY, VY, D, DF>;
     // the divergence watchdog stopped the run: nothing more to compute
     if (__ldcg(a.err) & DEV_ERR_NONFINITE) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -159,7 +164,8 @@ __global__ void __launch_bounds__(TX *TY)
             !mbar_wait_bounded(&empty[slot], (uint32_t)(((jj - C::NSL) / C::NSL) & 1), wait_ns))
             return false;
         const bool with_out = jj >= 2 * R;
-        mbar_arrive_expect_tx(&full[slot], C::HALO_BYTES + (with_out ? 3 * C::INT_BYTES : 0));
+        mbar_arrive_expect_tx(&full[slot],
+                              C::HALO_BYTES + (with_out ? C::NINT * C::INT_BYTES : 0));
         float *st = smem + slot * C::STAGE;
         tma_load_4d(st, &map_halo, &full[slot], x0 - C::RA, y0 - R, za - R + jj, wcur);
         if (with_out) {
@@ -167,6 +173,7 @@ __global__ void __launch_bounds__(TX *TY)
             tma_load_4d(st + C::HALO, &map_int, &full[slot], x0, y0, zo, wcur);
             tma_load_4d(st + C::HALO + C::INT, &map_int, &full[slot], x0, y0, zo, wprev);
             tma_load_4d(st + C::HALO + 2 * C::INT, &map_b, &full[slot], x0, y0, zo, 0);
+            if (DF) tma_load_4d(st + C::HALO + 3 * C::INT, &map_b, &full[slot], x0, y0, zo, 1);
         }
         issued = jj + 1;
         return true;
@@ -314,9 +321,16 @@ __global__ void __launch_bounds__(TX *TY)
                 const Q4 p = lds_q4(Pi + q);
                 const Q4 b = lds_q4(Bi + q);
                 const Q4 s = acc[0][v];
-                const f2 dyz = f2_splat(dpyv[v] + dz);
-                const f2 zl = f2_mul(f2_add(dpx_lo, dyz), b.lo);
-                const f2 zh = f2_mul(f2_add(dpx_hi, dyz), b.hi);
+                f2 zl, zh;
+                if constexpr (DF) {
+                    const Q4 zt = lds_q4(Bi + C::INT + q);
+                    zl = zt.lo;
+                    zh = zt.hi;
+                } else {
+                    const f2 dyz = f2_splat(dpyv[v] + dz);
+                    zl = f2_mul(f2_add(dpx_lo, dyz), b.lo);
+                    zh = f2_mul(f2_add(dpx_hi, dyz), b.hi);
+                }
                 f2 ol = f2_fma(f2_sub(one2, zl), f2_sub(c.lo, p.lo), c.lo);
                 f2 oh = f2_fma(f2_sub(one2, zh), f2_sub(c.hi, p.hi), c.hi);
                 ol = f2_fma(b.lo, s.lo, ol);
@@ -358,17 +372,37 @@ struct ConfigEntry {
     const char *name;
 };
 
-template <int R, int TX, int TY, int VY, int D, int U>
+template <int R, int TX, int TY, int VY, int D, int U, bool DF = false>
 ConfigEntry make_entry(const char *name) {
-    using C = AcCfg<R, TX, TY, VY, D>;
+    using C = AcCfg<R, TX, TY, VY, D, DF>;
     return ConfigEntry{R,       TX,    TY,    VY,    D,
-                       (const void *)&acoustic_step_kernel<R, TX, TY, VY, D, U>,
+                       (const void *)&acoustic_step_kernel<R, TX, TY, VY, D, U, DF>,
                        C::SMEM, C::BX, C::BY, C::PW, C::PH, C::THREADS, name};
 }
 
 #define FD_AC_ENTRY(R, TX, TY, VY, D, U)                                           \
     make_entry<R, TX, TY, VY, D, U>("acoustic_step<" #R "," #TX "," #TY "," #VY "," #D \
                                     "," #U ">")
+#define FD_AC_ENTRY_DF(R, TX, TY, VY, D, U)                                              \
+    make_entry<R, TX, TY, VY, D, U, true>("acoustic_step<" #R "," #TX "," #TY "," #VY "," #D \
+                                          "," #U ",damp field>")
+
+// 3-D damping field: one configuration per radius, the default one's.
+const ConfigEntry *config_table_df(int radius) {
+    static const ConfigEntry r1 = FD_AC_ENTRY_DF(1, 16, 16, 1, 4, 1);
+    static const ConfigEntry r2 = FD_AC_ENTRY_DF(2, 16, 16, 1, 4, 4);
+    static const ConfigEntry r4 = FD_AC_ENTRY_DF(4, 16, 8, 1, 4, 4);
+    static const ConfigEntry r6 = FD_AC_ENTRY_DF(6, 16, 8, 1, 3, 4);
+    static const ConfigEntry r8 = FD_AC_ENTRY_DF(8, 16, 8, 1, 1, 4);
+    switch (radius) {
+        case 1: return &r1;
+        case 2: return &r2;
+        case 4: return &r4;
+        case 6: return &r6;
+        case 8: return &r8;
+        default: return nullptr;
+    }
+}
 
 const ConfigEntry *config_table(int radius, int *count) {
     // Index 0 is the default; the others are kept for tuning sweeps
@@ -392,18 +426,22 @@ const ConfigEntry *config_table(int radius, int *count) {
         FD_AC_ENTRY(6, 16, 8, 1, 3, 4),  FD_AC_ENTRY(6, 16, 8, 1, 2, 4),
         FD_AC_ENTRY(6, 16, 16, 1, 3, 1), FD_AC_ENTRY(6, 8, 16, 1, 3, 1),
         FD_AC_ENTRY(6, 16, 8, 1, 2, 1),  FD_AC_ENTRY(6, 16, 8, 1, 3, 2),
-        FD_AC_ENTRY(6, 16, 8, 1, 4, 4),  FD_AC_ENTRY(6, 16, 8, 1, 1, 4)};
+        FD_AC_ENTRY(6, 16, 8, 1, 4, 4),  FD_AC_ENTRY(6, 16, 8, 1, 1, 4),
+        FD_AC_ENTRY(6, 16, 8, 1, 3, 1),  FD_AC_ENTRY(6, 16, 8, 1, 3, 3),
+        FD_AC_ENTRY(6, 16, 8, 1, 5, 6),  FD_AC_ENTRY(6, 16, 8, 1, 2, 3)};
     static const ConfigEntry r8[] = {
         FD_AC_ENTRY(8, 16, 8, 1, 1, 4),  FD_AC_ENTRY(8, 16, 8, 1, 2, 1),
         FD_AC_ENTRY(8, 16, 16, 1, 3, 1), FD_AC_ENTRY(8, 8, 16, 1, 3, 1),
         FD_AC_ENTRY(8, 16, 8, 1, 2, 4),  FD_AC_ENTRY(8, 16, 8, 1, 1, 2),
-        FD_AC_ENTRY(8, 8, 16, 1, 1, 4),  FD_AC_ENTRY(8, 16, 8, 1, 1, 8)};
+        FD_AC_ENTRY(8, 8, 16, 1, 1, 4),  FD_AC_ENTRY(8, 16, 8, 1, 1, 8),
+        FD_AC_ENTRY(8, 16, 8, 1, 3, 4),  FD_AC_ENTRY(8, 16, 8, 1, 3, 1),
+        FD_AC_ENTRY(8, 16, 8, 1, 2, 3),  FD_AC_ENTRY(8, 16, 8, 1, 2, 6)};
     switch (radius) {
         case 1: *count = 1; return r1;
         case 2: *count = 8; return r2;
         case 4: *count = 10; return r4;
-        case 6: *count = 8; return r6;
-        case 8: *count = 8; return r8;
+        case 6: *count = 12; return r6;
+        case 8: *count = 12; return r8;
         default: *count = 0; return nullptr;
     }
 }
@@ -422,15 +460,17 @@ int acoustic_default_config(int radius) {
 }
 
 fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots, int lps,
-                        float *wave, const float *bcoef, AcousticPlan *plan, int map_shots) {
+                        float *wave, const float *bcoef, AcousticPlan *plan, int map_shots,
+                        bool damp_field) {
     if (map_shots < nshots) map_shots = nshots;
     int n = 0;
     const ConfigEntry *tab = config_table(radius, &n);
     if (!tab) return set_error(FD_ERR_SO, "no acoustic kernel for radius %d", radius);
-    if (config < 0 || config >= n) config = acoustic_default_config(radius);
-    const ConfigEntry &e = tab[config];
+    if (config < 0 || config >= n || damp_field) config = acoustic_default_config(radius);
+    const ConfigEntry &e = damp_field ? *config_table_df(radius) : tab[config];
     plan->radius = radius;
     plan->config = config;
+    plan->damp_field = damp_field;
     plan->name = e.name;
     plan->smem = e.smem;
     plan->block = dim3(e.threads, 1, 1);
@@ -468,8 +508,9 @@ fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots,
     FD_TRY(make_tensor_map_4d(&plan->map_int, wave, L.nx, L.ny, L.nz, (uint64_t)map_shots * lps,
                               (uint64_t)L.nxp * 4, (uint64_t)L.plane * 4, (uint64_t)L.vol * 4,
                               e.bx, e.by, 1, 1));
-    return make_tensor_map_4d(&plan->map_b, bcoef, L.nx, L.ny, L.nz, 1, (uint64_t)L.nxp * 4,
-                              (uint64_t)L.plane * 4, (uint64_t)L.vol * 4, e.bx, e.by, 1, 1);
+    return make_tensor_map_4d(&plan->map_b, bcoef, L.nx, L.ny, L.nz, damp_field ? 2 : 1,
+                              (uint64_t)L.nxp * 4, (uint64_t)L.plane * 4, (uint64_t)L.vol * 4,
+                              e.bx, e.by, 1, 1);
 }
 
 fd_status acoustic_launch(const AcousticPlan &plan, const AcousticStepArgs &args,
@@ -490,8 +531,8 @@ fd_status acoustic_launch(const AcousticPlan &plan, const AcousticStepArgs &args
     if (!a.wait_ns) a.wait_ns = wait_limit_ns();
     void *params[] = {(void *)&plan.map_halo, (void *)&plan.map_int, (void *)&plan.map_b,
                       (void *)&a, (void *)&inj, (void *)&zchunk, (void *)&nzc};
-    FD_CUDA_TRY(cudaLaunchKernel(tab[plan.config].fn, plan.grid, plan.block, params, plan.smem,
-                                 stream));
+    const void *fn = plan.damp_field ? config_table_df(plan.radius)->fn : tab[plan.config].fn;
+    FD_CUDA_TRY(cudaLaunchKernel(fn, plan.grid, plan.block, params, plan.smem, stream));
     note_launch(stream);
     return FD_OK;
 }

@@ -463,11 +463,14 @@ GridDerived derive(const fd_grid *g, int so) {
 
 // ====================================================================== acoustic
 
+// damp_field: damp is a 3-D field [nz][ny][nx] instead of per-axis profiles;
+// the stencil kernel then reads zeta = damp b / dt per point.
 static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, int nt, int nshots,
                                        const float *m, const float *damp, int nsrc,
                                        const float *src_xyz, const float *src_wav, int nrec,
                                        const float *rec_xyz, float *rec_out, const float *u_init,
-                                       float *u_final, cudaStream_t caller) {
+                                       float *u_final, cudaStream_t caller,
+                                       bool damp_field = false) {
     FD_TRY(validate_common(grid, so, dt, nt, nshots, m, nsrc, src_xyz, src_wav, nrec, rec_xyz,
                            rec_out));
     const int R = so / 2;
@@ -477,7 +480,7 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     const int ndamp = L.nx + L.ny + L.nz;
     // two steps per launch needs four distinct levels per shot
     int t2_config = 0;
-    const bool tiled = use_time_tiling(R, nsrc, nt - 1, &t2_config);
+    const bool tiled = !damp_field && use_time_tiling(R, nsrc, nt - 1, &t2_config);
     const int lps = tiled ? 4 : 2;
 
     CallStream cs;
@@ -490,7 +493,7 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     MediumStats *dstats;
     int *counter;
     ws.add(&wave, (size_t)lps * nshots * L.vol);  // u levels per shot
-    ws.add(&bcoef, L.vol);                      // b = dt^2 / (m + damp dt/2)
+    ws.add(&bcoef, (damp_field ? 2 : 1) * (size_t)L.vol);  // b = dt^2 / (m + damp dt/2) [, zeta]
     ws.add(&dps, ndamp);                        // damping / dt
     ws.add(&src_tab, (size_t)nshots * nsrc);
     ws.add(&rec_tab, (size_t)nshots * nrec);
@@ -499,7 +502,7 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     Staged sm, sdamp, ssxyz, swav, srxyz;
     StagedOut srec;
     sm.plan(ws, m, dense);
-    sdamp.plan(ws, damp, damp ? ndamp : 0);
+    sdamp.plan(ws, damp, damp ? (damp_field ? dense : (size_t)ndamp) : 0);
     ssxyz.plan(ws, src_xyz, (size_t)nshots * nsrc * 3);
     swav.plan(ws, src_wav, (size_t)nshots * nt * nsrc);
     srxyz.plan(ws, rec_xyz, (size_t)nshots * nrec * 3);
@@ -512,9 +515,9 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     FD_STAGE(s, "acoustic: inputs staged");
 
     // ---- K0: coefficients, tables, validation
-    FD_CUDA_TRY(cudaMemsetAsync(bcoef, 0, (size_t)L.vol * 4, s));
+    FD_CUDA_TRY(cudaMemsetAsync(bcoef, 0, (damp_field ? 2 : 1) * (size_t)L.vol * 4, s));
     FD_TRY(init_medium_stats(dstats, s));
-    FD_TRY(setup_acoustic_coeffs(sm.dev, sdamp.dev, dt, L, bcoef, dps, dstats, s));
+    FD_TRY(setup_acoustic_coeffs(sm.dev, sdamp.dev, dt, L, bcoef, dps, dstats, s, damp_field));
     FD_STAGE(s, "acoustic: coefficients");
     for (int sh = 0; sh < nshots; ++sh) {
         FD_TRY(setup_sparse_table(ssxyz.dev ? ssxyz.dev + (size_t)sh * nsrc * 3 : nullptr, nsrc,
@@ -546,7 +549,8 @@ static fd_status acoustic_forward_impl(const fd_grid *grid, int so, double dt, i
     // ---- K1 plan and arguments
     AcousticPlan plan;
     FD_STAGE(s, "acoustic: initial state");
-    FD_TRY(acoustic_plan(R, g_acoustic_config[R], L, nshots, lps, wave, bcoef, &plan));
+    FD_TRY(acoustic_plan(R, g_acoustic_config[R], L, nshots, lps, wave, bcoef, &plan, 0,
+                         damp_field));
     FD_STAGE(s, plan.name);
     AcousticStepArgs a;
     memset(&a, 0, sizeof(a));
@@ -1575,10 +1579,17 @@ fd_status acoustic_forward_opts(const fd_grid *grid, int so, double dt, int nt, 
                                 float *u_final, const fd_acoustic_options *opts, void *stream) {
     fdsweep::clear_error();
     const int storage = opts ? opts->storage : FD_STORAGE_F32;
+    const int layout = opts ? opts->damp_layout : FD_DAMP_AXES;
+    if (layout != FD_DAMP_AXES && layout != FD_DAMP_FIELD)
+        return fdsweep::set_error(FD_ERR_ARG, "acoustic_forward_opts: damp_layout %d not in {0, 1}",
+                                  layout);
     if (storage == FD_STORAGE_F32)
         return fdsweep::acoustic_forward_impl(grid, so, dt, nt, nshots, m, damp, nsrc, src_xyz,
                                               src_wav, nrec, rec_xyz, rec_out, u_init, u_final,
-                                              (cudaStream_t)stream);
+                                              (cudaStream_t)stream, layout == FD_DAMP_FIELD);
+    if (layout == FD_DAMP_FIELD)
+        return fdsweep::set_error(FD_ERR_ARG,
+                                  "acoustic_forward_opts: a 3-D damping field needs FP32 storage");
     if (storage == FD_STORAGE_F16)
         return fdsweep::acoustic_forward_h_impl(grid, so, dt, nt, nshots, m, damp, nsrc, src_xyz,
                                                 src_wav, nrec, rec_xyz, rec_out, u_init, u_final,

@@ -99,6 +99,7 @@ struct AcousticPlan {
     dim3 grid, block;
     size_t smem = 0;
     int zchunk = 0, nzc = 1;
+    bool damp_field = false;  // the kernel variant that reads zeta per point
     const char *name = "";
 };
 
@@ -130,8 +131,11 @@ int acoustic_default_config(int radius);
 // `lps` levels per shot are addressable (buffers nshots * lps).  The launch
 // covers `nshots` shots; the tensor maps cover `map_shots` shots (default:
 // nshots) for callers that map launch shots to slots (slot_map).
+// damp_field: the damping is a 3-D field; bcoef then holds two fields, b and
+// zeta = damp b / dt ([2][vol]), and the default configuration is used.
 fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots, int lps,
-                        float *wave, const float *bcoef, AcousticPlan *plan, int map_shots = 0);
+                        float *wave, const float *bcoef, AcousticPlan *plan, int map_shots = 0,
+                        bool damp_field = false);
 fd_status acoustic_launch(const AcousticPlan &plan, const AcousticStepArgs &args,
                           cudaStream_t stream, const AcousticInject *inject = nullptr);
 
@@ -220,9 +224,12 @@ struct MediumStats {
 
 // b = dt^2 / (m + damp dt/2) in the padded layout; damp per-axis profiles
 // scaled by 1/dt into dps[nx + ny + nz].  m and damp are dense device arrays.
+// damp_field: damp is a 3-D field [nz][ny][nx]; bcoef then has two fields,
+// b and zeta = damp b / dt, and dps is zero.
 fd_status setup_acoustic_coeffs(const float *m, const float *damp, double dt,
                                 const WaveLayout &L, float *bcoef, float *dps,
-                                MediumStats *dev_stats, cudaStream_t stream);
+                                MediumStats *dev_stats, cudaStream_t stream,
+                                bool damp_field = false);
 // TTI extra fields: a = 1 + 2 eps, s = sqrt(1 + 2 delta), n = (nx, ny, nz).
 fd_status setup_tti_coeffs(const float *eps, const float *delta, const float *theta,
                            const float *phi, const WaveLayout &L, float *acoef, float *scoef,

@@ -106,10 +106,15 @@ __device__ __forceinline__ float div_two_float_rn(float A, float a, float X, flo
 // once (div_two_float_rn).  FP64 -- slow on this part -- remains for the
 // points that fail validation or lie outside the range where the two-float
 // steps are exact (m or a damping term negative, non-finite, or extreme).
+// With `zeta` non-null the damping is a 3-D field damp[nz][ny][nx] (d = damp
+// at the point) and zeta = fl(fl(d / dt) b) is stored beside b, the factor
+// the stencil kernel's damp-field variant reads instead of forming it from
+// per-axis profiles (the same two roundings as the profile path's
+// fl(fl(d_x/dt + (d_y/dt + d_z/dt)) b) when a single axis is damped).
 __global__ void acoustic_coeff_kernel(const float *__restrict__ m, const float *__restrict__ damp,
                                       double dt, float dt2_hi, float dt2_lo, float hdt_hi,
                                       float hdt_lo, WaveLayout L, float *__restrict__ bcoef,
-                                      StatsKeys *stats) {
+                                      float *__restrict__ zeta, StatsKeys *stats) {
     const int64_t rows = (int64_t)L.ny * L.nz;
     const double dt2 = dt * dt;
     float lmin = __int_as_float(0x7f800000), lmax = 0.f;
@@ -117,13 +122,16 @@ __global__ void acoustic_coeff_kernel(const float *__restrict__ m, const float *
     for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
         const int j = (int)(r % L.ny);
         const int k = (int)(r / L.ny);
-        const float dyf = damp ? damp[L.nx + j] : 0.f, dzf = damp ? damp[L.nx + L.ny + k] : 0.f;
+        const bool dense = zeta != nullptr;
+        const float dyf = damp && !dense ? damp[L.nx + j] : 0.f;
+        const float dzf = damp && !dense ? damp[L.nx + L.ny + k] : 0.f;
         const bool row_ok = dyf >= 0.f && dyf <= 1.0e30f && dzf >= 0.f && dzf <= 1.0e30f;
         const float *mrow = m + r * L.nx;
+        const float *drow = dense && damp ? damp + r * L.nx : nullptr;
         float *brow = bcoef + (int64_t)k * L.plane + (int64_t)j * L.nxp;
         for (int i = threadIdx.x; i < L.nx; i += blockDim.x) {
             const float mv = mrow[i];
-            const float dxf = damp ? damp[i] : 0.f;
+            const float dxf = drow ? drow[i] : (damp && !dense ? damp[i] : 0.f);
             lmin = fminf(lmin, mv);
             lmax = fmaxf(lmax, mv);
             if (row_ok && dxf >= 0.f && dxf <= 1.0e30f && mv >= 1.17549435e-38f &&
@@ -144,6 +152,9 @@ __global__ void acoustic_coeff_kernel(const float *__restrict__ m, const float *
                     bad = DEV_ERR_MEDIUM;
                 brow[i] = (float)(dt2 * recip_newton((double)mv + 0.5 * d * dt));
             }
+            if (dense)
+                zeta[(int64_t)k * L.plane + (int64_t)j * L.nxp + i] =
+                    __fmul_rn((float)((double)dxf / dt), brow[i]);
         }
     }
     lmin = warp_min(lmin);
@@ -277,17 +288,19 @@ fd_status init_medium_stats(MediumStats *dev_stats, cudaStream_t stream) {
 
 fd_status setup_acoustic_coeffs(const float *m, const float *damp, double dt,
                                 const WaveLayout &L, float *bcoef, float *dps,
-                                MediumStats *dev_stats, cudaStream_t stream) {
+                                MediumStats *dev_stats, cudaStream_t stream, bool damp_field) {
     StatsKeys *keys = reinterpret_cast<StatsKeys *>(dev_stats);
     const double dt2 = dt * dt, hdt = 0.5 * dt;
     const float dt2_hi = (float)dt2, hdt_hi = (float)hdt;
     const float dt2_lo = (float)(dt2 - (double)dt2_hi), hdt_lo = (float)(hdt - (double)hdt_hi);
     acoustic_coeff_kernel<<<grid_for((int64_t)L.ny * L.nz * 256, 256), 256, 0, stream>>>(
-        m, damp, dt, dt2_hi, dt2_lo, hdt_hi, hdt_lo, L, bcoef, keys);
+        m, damp, dt, dt2_hi, dt2_lo, hdt_hi, hdt_lo, L, bcoef, damp_field ? bcoef + L.vol : nullptr,
+        keys);
     FD_CUDA_TRY(cudaGetLastError());
     note_launch(stream);
     const int nd = L.nx + L.ny + L.nz;
-    damp_scale_kernel<<<(nd + 255) / 256, 256, 0, stream>>>(damp, nd, dt, dps);
+    damp_scale_kernel<<<(nd + 255) / 256, 256, 0, stream>>>(damp_field ? nullptr : damp, nd, dt,
+                                                            dps);
     FD_CUDA_TRY(cudaGetLastError());
     note_launch(stream);
     return FD_OK;
