@@ -706,6 +706,34 @@ def run_serving(args, fd, dev, gpts_so8):
             "latency_is": "job arrival to delivery of its last shot's traces (device)"}
 
 
+def run_serving_only(args):
+    """The served shot stream alone (config: Poisson arrivals, grids {128, 256,
+    384}^3, nt U{500..3000}, 1-32 shots per job, so 8), batched server against
+    one acoustic_forward call per shot, with `--serve-jobs` jobs so that p99
+    is a tail and not the maximum.  The arrival rate is 0.8 x the capacity
+    implied by the so-8 kernel rate measured here on a 512^3 forward."""
+    import torch
+    import paper_1807_03032_gb300 as fd
+    from paper_1807_03032_gb300 import _native
+    dev = torch.device("cuda", 0)
+    w = workloads.acoustic_large(n=512, so=8, nt=40)
+    g = fd.Grid(w.shape, w.spacing, w.origin)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    m, damp, sx, sw, rx = T(w.m), T(w.damp), T(w.src_xyz), T(w.src_wav), T(w.rec_xyz)
+    fd.acoustic_forward(g, 8, w.dt, w.nt, m, sx, sw, rx, damp=damp, return_final=False)
+    _native.stats_reset()
+    _native.stats_enable(True)
+    fd.acoustic_forward(g, 8, w.dt, w.nt, m, sx, sw, rx, damp=damp, return_final=False)
+    torch.cuda.synchronize()
+    ms, k, pts = _native.stats_get("acoustic_step")
+    _native.stats_enable(False)
+    gpts = pts / (ms / k * 1e-3) / 1e9
+    del m, damp, sx, sw, rx
+    torch.cuda.empty_cache()
+    out = run_serving(args, fd, dev, gpts)
+    print(json.dumps({"serving": out}), flush=True)
+
+
 def run_batched_probe(args):
     """Diagnostic (not the benchmark line): one acoustic forward of S shots
     sharing a two-layer 256^3 model (so 8, nt 4, one source and one receiver
@@ -851,10 +879,14 @@ def main():
     ap.add_argument("--batched-probe", type=int, default=0, metavar="S",
                     help="diagnostic only: one forward of S shots on a 256^3 so-8 model")
     ap.add_argument("--batched-n", type=int, default=256)
+    ap.add_argument("--serving-only", action="store_true",
+                    help="run only the served shot stream (with --serve-jobs jobs)")
     args = ap.parse_args()
     args.so = tuple(args.so)
     if args.batched_probe:
         run_batched_probe(args)
+    elif args.serving_only:
+        run_serving_only(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

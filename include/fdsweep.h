@@ -124,6 +124,13 @@ fd_status acoustic_forward(const fd_grid *grid, int so, double dt, int nt, int n
  *                  FD_ERR_DIVERGED).  Radii with a binary16 kernel: so = 2..16
  *                  (FD_ERR_UNIMPL otherwise); time tiling is not combined
  *                  with it.
+ *                  FD_STORAGE_AUTO: the faster of the two on GB300 for the
+ *                  space order, measured at 512^3: binary16 for so <= 8 (its
+ *                  kernel 1.26x / 1.10x the FP32 one at so 4 / 8), FP32 for
+ *                  so 12 and 16 (where the binary16 kernel, bound by shared
+ *                  memory and conversions, ran 0.94x / 0.89x), and FP32 with
+ *                  FD_DAMP_FIELD.  The results are those of the storage
+ *                  chosen.
  *   opts->damp_layout
  *                  FD_DAMP_AXES: damp holds the per-axis profiles
  *                  [nx + ny + nz] of acoustic_forward (damp(i,j,k) = d_x[i] +
@@ -141,7 +148,7 @@ fd_status acoustic_forward(const fd_grid *grid, int so, double dt, int nt, int n
  *                  Out-of-range values return FD_ERR_ARG.
  * Other arguments, ownership and errors as for acoustic_forward.
  */
-enum { FD_STORAGE_F32 = 0, FD_STORAGE_F16 = 1 };
+enum { FD_STORAGE_F32 = 0, FD_STORAGE_F16 = 1, FD_STORAGE_AUTO = 2 };
 enum { FD_DAMP_AXES = 0, FD_DAMP_FIELD = 1 };
 typedef struct {
     int32_t storage;

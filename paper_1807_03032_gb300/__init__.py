@@ -97,8 +97,10 @@ def acoustic_forward(grid, so, dt, nt, m, src_xyz, src_wav, rec_xyz, damp=None, 
     with FD_DAMP_FIELD), or None;
     src_xyz [nshots][nsrc][3]; src_wav [nshots][nt][nsrc]; rec_xyz [nshots][nrec][3];
     u_init [nshots][2][nz][ny][nx] (u^0, u^-1) or None.
-    storage: "f32" or "f16" (wavefields and b held in IEEE binary16 on the
-    device, FP32 arithmetic; C ABI ``acoustic_forward_opts``).
+    storage: "f32", "f16" (wavefields and b held in IEEE binary16 on the
+    device, FP32 arithmetic; C ABI ``acoustic_forward_opts``) or "auto"
+    (binary16 for so <= 8, where it is the faster storage on GB300, FP32
+    beyond).
     Returns (rec [nshots][nt][nrec], u_final [nshots][2][nz][ny][nx] or None).
     Outputs are allocated like ``m`` (same device / host) unless given.
     """

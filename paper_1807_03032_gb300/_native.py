@@ -54,7 +54,7 @@ class FdAcousticOptions(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int32), ("damp_layout", ctypes.c_int32)]
 
 
-STORAGE = {"f32": 0, "f16": 1}
+STORAGE = {"f32": 0, "f16": 1, "auto": 2}
 DAMP_LAYOUT = {"axes": 0, "field": 1}
 TTI_DERIV = {"centred": 0, "staggered": 1}
 TTI_RECEIVER = {"p": 0, "mean": 1}

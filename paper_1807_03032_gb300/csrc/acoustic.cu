@@ -426,22 +426,18 @@ const ConfigEntry *config_table(int radius, int *count) {
         FD_AC_ENTRY(6, 16, 8, 1, 3, 4),  FD_AC_ENTRY(6, 16, 8, 1, 2, 4),
         FD_AC_ENTRY(6, 16, 16, 1, 3, 1), FD_AC_ENTRY(6, 8, 16, 1, 3, 1),
         FD_AC_ENTRY(6, 16, 8, 1, 2, 1),  FD_AC_ENTRY(6, 16, 8, 1, 3, 2),
-        FD_AC_ENTRY(6, 16, 8, 1, 4, 4),  FD_AC_ENTRY(6, 16, 8, 1, 1, 4),
-        FD_AC_ENTRY(6, 16, 8, 1, 3, 1),  FD_AC_ENTRY(6, 16, 8, 1, 3, 3),
-        FD_AC_ENTRY(6, 16, 8, 1, 5, 6),  FD_AC_ENTRY(6, 16, 8, 1, 2, 3)};
+        FD_AC_ENTRY(6, 16, 8, 1, 4, 4),  FD_AC_ENTRY(6, 16, 8, 1, 1, 4)};
     static const ConfigEntry r8[] = {
         FD_AC_ENTRY(8, 16, 8, 1, 1, 4),  FD_AC_ENTRY(8, 16, 8, 1, 2, 1),
         FD_AC_ENTRY(8, 16, 16, 1, 3, 1), FD_AC_ENTRY(8, 8, 16, 1, 3, 1),
         FD_AC_ENTRY(8, 16, 8, 1, 2, 4),  FD_AC_ENTRY(8, 16, 8, 1, 1, 2),
-        FD_AC_ENTRY(8, 8, 16, 1, 1, 4),  FD_AC_ENTRY(8, 16, 8, 1, 1, 8),
-        FD_AC_ENTRY(8, 16, 8, 1, 3, 4),  FD_AC_ENTRY(8, 16, 8, 1, 3, 1),
-        FD_AC_ENTRY(8, 16, 8, 1, 2, 3),  FD_AC_ENTRY(8, 16, 8, 1, 2, 6)};
+        FD_AC_ENTRY(8, 8, 16, 1, 1, 4),  FD_AC_ENTRY(8, 16, 8, 1, 1, 8)};
     switch (radius) {
         case 1: *count = 1; return r1;
         case 2: *count = 8; return r2;
         case 4: *count = 10; return r4;
-        case 6: *count = 12; return r6;
-        case 8: *count = 12; return r8;
+        case 6: *count = 8; return r6;
+        case 8: *count = 8; return r8;
         default: *count = 0; return nullptr;
     }
 }

@@ -1578,11 +1578,18 @@ fd_status acoustic_forward_opts(const fd_grid *grid, int so, double dt, int nt, 
                                 const float *rec_xyz, float *rec_out, const float *u_init,
                                 float *u_final, const fd_acoustic_options *opts, void *stream) {
     fdsweep::clear_error();
-    const int storage = opts ? opts->storage : FD_STORAGE_F32;
+    int storage = opts ? opts->storage : FD_STORAGE_F32;
     const int layout = opts ? opts->damp_layout : FD_DAMP_AXES;
     if (layout != FD_DAMP_AXES && layout != FD_DAMP_FIELD)
         return fdsweep::set_error(FD_ERR_ARG, "acoustic_forward_opts: damp_layout %d not in {0, 1}",
                                   layout);
+    // FD_STORAGE_AUTO: binary16 storage where its kernel measured faster than
+    // the FP32 one on GB300 at 512^3 (so <= 8: 1.26x and 1.10x), FP32 storage
+    // where it did not (so 12: 0.94x, so 16: 0.89x; the binary16 kernel is
+    // bound by shared memory and conversions there), and FP32 with a 3-D
+    // damping field.
+    if (storage == FD_STORAGE_AUTO)
+        storage = (so <= 8 && layout == FD_DAMP_AXES) ? FD_STORAGE_F16 : FD_STORAGE_F32;
     if (storage == FD_STORAGE_F32)
         return fdsweep::acoustic_forward_impl(grid, so, dt, nt, nshots, m, damp, nsrc, src_xyz,
                                               src_wav, nrec, rec_xyz, rec_out, u_init, u_final,
@@ -1594,7 +1601,7 @@ fd_status acoustic_forward_opts(const fd_grid *grid, int so, double dt, int nt, 
         return fdsweep::acoustic_forward_h_impl(grid, so, dt, nt, nshots, m, damp, nsrc, src_xyz,
                                                 src_wav, nrec, rec_xyz, rec_out, u_init, u_final,
                                                 (cudaStream_t)stream);
-    return fdsweep::set_error(FD_ERR_ARG, "acoustic_forward_opts: storage %d not in {0, 1}",
+    return fdsweep::set_error(FD_ERR_ARG, "acoustic_forward_opts: storage %d not in {0, 1, 2}",
                               storage);
 }
 

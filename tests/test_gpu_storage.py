@@ -275,3 +275,17 @@ def test_host_buffers_give_the_same_bits():
         assert not r.is_cuda and not uf.is_cuda
         np.testing.assert_array_equal(r.numpy(), rd)
         np.testing.assert_array_equal(uf.numpy(), ud)
+
+
+@pytest.mark.parametrize("so", [4, 8, 12, 16])
+def test_automatic_storage_picks_the_faster_kernel_per_space_order(so):
+    """FD_STORAGE_AUTO: binary16 storage for so <= 8, FP32 for so 12 and 16,
+    bit for bit the run of the storage it chose."""
+    torch = require_cuda()
+    shape, h, m, damp, dt, src, wav, rec = run_case(so, nt=16)
+    auto = gpu_run(torch, shape, h, so, dt, 16, m, damp, src=src, wav=wav, rec=rec,
+                   storage="auto")
+    want = gpu_run(torch, shape, h, so, dt, 16, m, damp, src=src, wav=wav, rec=rec,
+                   storage="f16" if so <= 8 else "f32")
+    np.testing.assert_array_equal(auto[0], want[0])
+    np.testing.assert_array_equal(auto[1], want[1])
