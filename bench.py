@@ -377,6 +377,12 @@ def run_ours(args):
         storage_f16 = run_storage_f16(args, fd, _native, g, w, m, damp, sxyz, swav, rxyz,
                                       stream, peak, per_so)
 
+    # ---------------------------------------------------------------- 3-D damping field
+    damp_field = None
+    if not args.no_damp_field:
+        damp_field = run_damp_field(args, fd, _native, g, w, m, damp, sxyz, swav, rxyz, stream,
+                                    peak)
+
     # ---------------------------------------------------------------- TTI
     tti = None
     if not args.no_tti:
@@ -421,6 +427,7 @@ def run_ours(args):
             "e2e": e2e,
             "cpu_baseline": cpu,
             "storage_f16": storage_f16,
+            "damp_field": damp_field,
             "tti": tti,
             "fwi_gradient": fwi,
             "serving": serving,
@@ -476,6 +483,46 @@ def run_storage_f16(args, fd, _native, g, w, m, damp, sxyz, swav, rxyz, stream, 
         if k32:
             row["kernel_speedup_vs_f32"] = round(kg / k32, 3)
         out["per_so"][str(so)] = row
+    return out
+
+
+def run_damp_field(args, fd, _native, g, w, m, damp, sxyz, swav, rxyz, stream, peak):
+    """The same forward runs with the damping given as a 3-D field (the
+    workload's separable sponge expanded point by point; acoustic_forward_opts
+    with FD_DAMP_FIELD): the stencil kernel then reads zeta = damp b / dt per
+    point, 20 algorithmic bytes per point.  Kernel rate, its HBM fraction,
+    and the distance of its traces from the profile path's."""
+    import torch
+    n = w.shape[0]
+    dh = np.asarray(w.damp, dtype=np.float64)
+    field = (dh[2 * n:, None, None] + dh[n:2 * n][None, :, None] + dh[:n][None, None, :])
+    d3 = torch.from_numpy(np.ascontiguousarray(field, dtype=np.float32)).to(m.device)
+    del field
+    nrec = rxyz.shape[1]
+    ra = torch.empty((1, w.nt, nrec), dtype=torch.float32, device=m.device)
+    rf = torch.empty_like(ra)
+    out = {"what": "acoustic_forward_opts with FD_DAMP_FIELD: the separable sponge given as a "
+                   "3-D field; the kernel reads zeta = damp b / dt per point",
+           "bytes_per_point": 20, "per_so": {}}
+    for so in args.so:
+        fd.acoustic_forward(g, so, w.dt, w.nt, m, sxyz, swav, rxyz, damp=damp, rec_out=ra,
+                            return_final=False)
+        _native.stats_reset()
+        _native.stats_enable(True)
+        fd.acoustic_forward(g, so, w.dt, w.nt, m, sxyz, swav, rxyz, damp=d3, rec_out=rf,
+                            return_final=False, damp_layout="field")
+        torch.cuda.synchronize()
+        kms, nl, npts = _native.stats_get("acoustic_step")
+        _native.stats_enable(False)
+        per = kms / max(nl, 1)
+        gbs = 20.0 * npts / (per * 1e-3) / 1e9
+        rel = float(torch.linalg.vector_norm((rf - ra).double()) /
+                    torch.linalg.vector_norm(ra.double()))
+        out["per_so"][str(so)] = {"kernel_gpts": round(npts / (per * 1e-3) / 1e9, 2),
+                                  "kernel_gbs": round(gbs, 1), "kernel_frac": round(gbs / peak, 4),
+                                  "traces_rel_l2_vs_profiles": float(f"{rel:.3e}")}
+    del d3
+    torch.cuda.empty_cache()
     return out
 
 
@@ -670,7 +717,8 @@ def run_serving(args, fd, dev, gpts_so8):
     arrivals; rate = 0.8 x the capacity implied by the measured so-8 kernel
     throughput of this run."""
     import torch
-    from paper_1807_03032_gb300.serving import Server, latency_stats, one_shot_per_launch
+    from paper_1807_03032_gb300.serving import Server, checksum_and_drop, latency_stats, \
+        one_shot_per_launch
     sizes = (128, 256, 384)
     mean_pts = np.mean([n ** 3 for n in sizes]) * 1750.0 * 16.5
     capacity = gpts_so8 * 1e9 / mean_pts
@@ -679,7 +727,7 @@ def run_serving(args, fd, dev, gpts_so8):
     nshots = sum(len(j.shots) for j in jobs)
     pts = sum(j.model.grid.shape[0] ** 3 * (s.nt - 1) for j in jobs for s in j.shots)
     srv = Server(hbm_budget=int(args.serve_budget_gb * (1 << 30)), max_slots=32, chunk=32,
-                 max_nsrc=1, max_nrec=128 * 128)
+                 max_nsrc=1, max_nrec=128 * 128, deliver=checksum_and_drop)
     t0 = time.perf_counter()
     srv.run(jobs)
     make = time.perf_counter() - t0
@@ -693,9 +741,13 @@ def run_serving(args, fd, dev, gpts_so8):
             s.traces = None
         j.done_at = None
     torch.cuda.empty_cache()
+    sums = [s.checksum for j in jobs for s in j.shots]
     t0 = time.perf_counter()
-    one_shot_per_launch(jobs)
+    one_shot_per_launch(jobs, deliver=checksum_and_drop)
     make_b = time.perf_counter() - t0
+    # the same traces from both paths (sums of squares, relative)
+    agree = max(abs(float(a) - float(s.checksum)) / max(float(s.checksum), 1e-300)
+                for a, s in zip(sums, (s for j in jobs for s in j.shots)))
     base = {"shots_per_s": round(nshots / make_b, 3), "gpts": round(pts / make_b / 1e9, 2),
             "makespan_s": round(make_b, 2), **{k: round(v, 3) for k, v in latency_stats(jobs).items()}}
     return {"workload": f"{len(jobs)} jobs / {nshots} shots, Poisson arrivals at "
@@ -703,6 +755,7 @@ def run_serving(args, fd, dev, gpts_so8):
                         f"rate {gpts_so8:.0f} GPts/s), grids {{128,256,384}}^3, nt U{{500..3000}}, "
                         f"1-32 shots per job, so 8, 128x128 receivers",
             "batched": served, "one_shot_per_launch": base,
+            "traces_sum_of_squares_max_rel_diff": float(f"{agree:.3e}"),
             "latency_is": "job arrival to delivery of its last shot's traces (device)"}
 
 
@@ -870,6 +923,8 @@ def main():
                     help="fd_set_time_tiling mode for every space order (-1 automatic, "
                          "0 off, 1 + k two-step kernel configuration k)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-damp-field", action="store_true",
+                    help="skip the 3-D damping-field runs")
     ap.add_argument("--no-fwi", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=10)

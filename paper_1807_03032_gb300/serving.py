@@ -122,6 +122,15 @@ class Shot:
     rec_xyz: object    # CUDA tensor [nrec][3]
     traces: object = None
     done_at: Optional[float] = None
+    checksum: object = None  # set by a deliver callback that drops the traces
+
+
+def checksum_and_drop(job, shot):
+    """A deliver callback for long streams: keeps the sum of squares of the
+    shot's traces (a device scalar) and frees the traces, so that the device
+    memory held by delivered results stays bounded."""
+    shot.checksum = shot.traces.double().square().sum()
+    shot.traces = None
 
 
 @dataclass(eq=False)
@@ -156,11 +165,14 @@ class Server:
     max_slots: slots per engine (shots of one model in flight).
     chunk: time steps per engine step between scheduling decisions (even).
     engine_factory: builds an engine for a model (tests inject a fake).
+    deliver: called as deliver(job, shot) once a shot's traces are complete
+    (the consumer; by default the traces stay on the shot).
     """
 
     def __init__(self, hbm_budget, max_slots=32, chunk=32, max_nsrc=1, max_nrec=16384,
                  engine_factory: Optional[Callable] = None, footprint_fn: Optional[Callable] = None,
-                 clock: Callable = time.perf_counter):
+                 clock: Callable = time.perf_counter, deliver: Optional[Callable] = None):
+        self.deliver = deliver
         self.budget = int(hbm_budget)
         self.max_slots = max_slots
         self.chunk = chunk + (chunk & 1)
@@ -241,6 +253,8 @@ class Server:
                     st.finishing.discard(s)
                     st.engine.release(s)
                     shot.done_at = now
+                    if self.deliver is not None:
+                        self.deliver(job, shot)
                     job._left -= 1
                     if job._left == 0:
                         job.done_at = now
@@ -297,9 +311,11 @@ class Server:
 
 # ---------------------------------------------------------------- baseline
 
-def one_shot_per_launch(jobs, clock: Callable = time.perf_counter):
+def one_shot_per_launch(jobs, clock: Callable = time.perf_counter,
+                        deliver: Optional[Callable] = None):
     """Every shot as its own acoustic_forward call, jobs in arrival order
-    (single server).  Sets shot.traces / done_at and job.done_at."""
+    (single server).  Sets shot.traces / done_at and job.done_at, and calls
+    deliver(job, shot) for every shot of a job once the job is done."""
     import torch
     t0 = clock()
     for job in sorted(jobs, key=lambda j: j.arrival):
@@ -317,6 +333,9 @@ def one_shot_per_launch(jobs, clock: Callable = time.perf_counter):
             shot.done_at = clock() - t0
         torch.cuda.synchronize()
         job.done_at = clock() - t0
+        if deliver is not None:
+            for shot in job.shots:
+                deliver(job, shot)
     return jobs
 
 

@@ -111,3 +111,28 @@ def test_model_larger_than_budget_is_rejected():
                  engine_factory=lambda md: FakeEngine(md, 4), footprint_fn=lambda md: 100)
     with pytest.raises(ValueError):
         srv.run(jobs)
+
+
+def test_deliver_callback_receives_every_finished_shot_once():
+    """With a deliver callback (the consumer of a long stream), every shot is
+    handed over exactly once, after its traces are complete; the provided
+    checksum_and_drop keeps the sum of squares and frees the traces."""
+    from paper_1807_03032_gb300.serving import checksum_and_drop
+    jobs = make_jobs(10, seed=3)
+    seen = []
+
+    def deliver(job, shot):
+        tag = float(shot.src_wav[0, 0])
+        assert torch.all(shot.traces == tag)
+        want = float((shot.traces.double() ** 2).sum())
+        seen.append(id(shot))
+        checksum_and_drop(job, shot)
+        assert shot.traces is None and float(shot.checksum) == want
+
+    srv = Server(hbm_budget=300, max_slots=4, chunk=8,
+                 engine_factory=lambda md: FakeEngine(md, 4), footprint_fn=lambda md: 100,
+                 deliver=deliver)
+    srv.run(jobs)
+    srv.close()
+    all_shots = [id(s) for j in jobs for s in j.shots]
+    assert sorted(seen) == sorted(all_shots)
