@@ -412,9 +412,12 @@ int64_t fd_launch_count(void);
  * wait is a single non-blocking test, so the waits give up on copies that are
  * merely in flight, the call returns FD_ERR_TIMEOUT and the device stays
  * usable (the copies already issued are still waited for, with their own
- * limit, before a stopped kernel exits).  Process-wide; it
- * applies to launches enqueued after the call (a CUDA graph keeps the limit it
- * was captured with).
+ * limit, before a stopped kernel exits).  Process-wide; it applies to the
+ * stencil kernel's default launch configuration with per-axis damping (a
+ * variant of it that reads the limit is launched while the setting is
+ * non-zero, so the production kernel keeps a constant limit), and to launches
+ * enqueued after the call (a CUDA graph keeps the variant it was captured
+ * with).
  */
 fd_status fd_set_wait_limit_ns(int64_t ns);
 

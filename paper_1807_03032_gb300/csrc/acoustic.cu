@@ -108,8 +108,12 @@ __device__ __noinline__ void inject_column(const AcousticStepArgs *a, const Acou
 // U: unroll factor of the plane loop.  The pending-output registers shift by
 // one plane per iteration; unrolling by U turns U - 1 of every U shifts into
 // register renaming instead of moves (U = 2R removes them all).
-template <int R, int TX, int TY, int VY, int D, int U, bool DF>
-__global__ void __launch_bounds__(TX *TY)
+// WL: the pipeline waits take their limit from the arguments (the
+// failure-injection setting of fd_set_wait_limit_ns); otherwise it is the
+// constant 2 s, which keeps the limit out of the plane loop's registers (a
+// limit read at run time cost 13 % at so 8).
+template <int R, int TX, int TY, int VY, int D, int U, bool DF, int MINB = 0, bool WL = false>
+__global__ void __launch_bounds__(TX *TY, MINB)
     acoustic_step_kernel(const __grid_constant__ CUtensorMap map_halo,
                          const __grid_constant__ CUtensorMap map_int,
                          const __grid_constant__ CUtensorMap map_b,
@@ -139,7 +143,7 @@ __global__ void __launch_bounds__(TX *TY)
     const int wcur = shot * a.lps + a.lev_cur, wprev = shot * a.lps + a.lev_prev;
     const int wout = shot * a.lps + a.lev_out;
     const int gx = x0 + 4 * tx;
-    const uint64_t wait_ns = a.wait_ns ? a.wait_ns : 2000000000ull;
+    const uint64_t wait_ns = WL ? (a.wait_ns ? a.wait_ns : 2000000000ull) : 2000000000ull;
 
     if (tid == 0) {
         prefetch_tensormap(&map_halo);
@@ -372,28 +376,55 @@ struct ConfigEntry {
     const char *name;
 };
 
-template <int R, int TX, int TY, int VY, int D, int U, bool DF = false>
+template <int R, int TX, int TY, int VY, int D, int U, bool DF = false, int MINB = 0,
+          bool WL = false>
 ConfigEntry make_entry(const char *name) {
     using C = AcCfg<R, TX, TY, VY, D, DF>;
     return ConfigEntry{R,       TX,    TY,    VY,    D,
-                       (const void *)&acoustic_step_kernel<R, TX, TY, VY, D, U, DF>,
+                       (const void *)&acoustic_step_kernel<R, TX, TY, VY, D, U, DF, MINB, WL>,
                        C::SMEM, C::BX, C::BY, C::PW, C::PH, C::THREADS, name};
 }
 
 #define FD_AC_ENTRY(R, TX, TY, VY, D, U)                                           \
     make_entry<R, TX, TY, VY, D, U>("acoustic_step<" #R "," #TX "," #TY "," #VY "," #D \
                                     "," #U ">")
-#define FD_AC_ENTRY_DF(R, TX, TY, VY, D, U)                                              \
-    make_entry<R, TX, TY, VY, D, U, true>("acoustic_step<" #R "," #TX "," #TY "," #VY "," #D \
-                                          "," #U ",damp field>")
+#define FD_AC_ENTRY_DF(R, TX, TY, VY, D, U, MB)                                              \
+    make_entry<R, TX, TY, VY, D, U, true, MB>("acoustic_step<" #R "," #TX "," #TY "," #VY "," #D \
+                                              "," #U ",damp field>")
 
-// 3-D damping field: one configuration per radius, the default one's.
+#define FD_AC_ENTRY_WL(R, TX, TY, VY, D, U)                                                 \
+    make_entry<R, TX, TY, VY, D, U, false, 0, true>("acoustic_step<" #R "," #TX "," #TY "," #VY \
+                                                    "," #D "," #U ",wait limit>")
+
+// The default configuration of each radius with the wait limit taken from the
+// arguments: launched instead of it while fd_set_wait_limit_ns is set.
+const ConfigEntry *config_table_wl(int radius) {
+    static const ConfigEntry r1 = FD_AC_ENTRY_WL(1, 16, 16, 1, 4, 1);
+    static const ConfigEntry r2 = FD_AC_ENTRY_WL(2, 16, 16, 1, 4, 4);
+    static const ConfigEntry r4 = FD_AC_ENTRY_WL(4, 16, 8, 1, 4, 4);
+    static const ConfigEntry r6 = FD_AC_ENTRY_WL(6, 16, 8, 1, 3, 4);
+    static const ConfigEntry r8 = FD_AC_ENTRY_WL(8, 16, 8, 1, 1, 4);
+    switch (radius) {
+        case 1: return &r1;
+        case 2: return &r2;
+        case 4: return &r4;
+        case 6: return &r6;
+        case 8: return &r8;
+        default: return nullptr;
+    }
+}
+
+// 3-D damping field: one configuration per radius, the default one's tiles,
+// with the prefetch depth and register bound chosen so that four CTAs fit
+// on an SM despite the fourth interior tile per stage: with fewer, the 512
+// columns of a 512^3 launch need two waves of 456 CTAs (measured: so 8 and
+// 12 at 0.6 of the copy bandwidth with the default depths).
 const ConfigEntry *config_table_df(int radius) {
-    static const ConfigEntry r1 = FD_AC_ENTRY_DF(1, 16, 16, 1, 4, 1);
-    static const ConfigEntry r2 = FD_AC_ENTRY_DF(2, 16, 16, 1, 4, 4);
-    static const ConfigEntry r4 = FD_AC_ENTRY_DF(4, 16, 8, 1, 4, 4);
-    static const ConfigEntry r6 = FD_AC_ENTRY_DF(6, 16, 8, 1, 3, 4);
-    static const ConfigEntry r8 = FD_AC_ENTRY_DF(8, 16, 8, 1, 1, 4);
+    static const ConfigEntry r1 = FD_AC_ENTRY_DF(1, 16, 16, 1, 4, 1, 0);
+    static const ConfigEntry r2 = FD_AC_ENTRY_DF(2, 16, 16, 1, 4, 4, 0);
+    static const ConfigEntry r4 = FD_AC_ENTRY_DF(4, 16, 8, 1, 3, 4, 0);
+    static const ConfigEntry r6 = FD_AC_ENTRY_DF(6, 16, 8, 1, 2, 4, 4);
+    static const ConfigEntry r8 = FD_AC_ENTRY_DF(8, 16, 8, 1, 1, 4, 4);
     switch (radius) {
         case 1: return &r1;
         case 2: return &r2;
@@ -498,6 +529,8 @@ fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots,
     plan->nzc = nzc;
     plan->smem = e.smem + (size_t)zchunk * 4;
     FD_TRY(raise_smem_limit(e.fn, plan->smem));
+    if (!damp_field && config == acoustic_default_config(radius))
+        FD_TRY(raise_smem_limit(config_table_wl(radius)->fn, plan->smem));
     FD_TRY(make_tensor_map_4d(&plan->map_halo, wave, L.nx, L.ny, L.nz, (uint64_t)map_shots * lps,
                               (uint64_t)L.nxp * 4, (uint64_t)L.plane * 4, (uint64_t)L.vol * 4,
                               e.pw, e.ph, 1, 1));
@@ -527,7 +560,11 @@ fd_status acoustic_launch(const AcousticPlan &plan, const AcousticStepArgs &args
     if (!a.wait_ns) a.wait_ns = wait_limit_ns();
     void *params[] = {(void *)&plan.map_halo, (void *)&plan.map_int, (void *)&plan.map_b,
                       (void *)&a, (void *)&inj, (void *)&zchunk, (void *)&nzc};
-    const void *fn = plan.damp_field ? config_table_df(plan.radius)->fn : tab[plan.config].fn;
+    const void *fn = tab[plan.config].fn;
+    if (plan.damp_field)
+        fn = config_table_df(plan.radius)->fn;
+    else if (a.wait_ns != 0 && plan.config == acoustic_default_config(plan.radius))
+        fn = config_table_wl(plan.radius)->fn;  // same tiles, ring and shared memory
     FD_CUDA_TRY(cudaLaunchKernel(fn, plan.grid, plan.block, params, plan.smem, stream));
     note_launch(stream);
     return FD_OK;
