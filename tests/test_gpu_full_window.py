@@ -6,7 +6,7 @@ FP32 rounding accumulates over those steps, so parity is checked here on the
 same recipes for the same simulated time: at 128^3 (border scaled with the
 grid: 10 points) for the full window at every space order, and at 512^3 for
 the first 50 steps from a smooth random state, both against the FP64 oracle.
-Besides the relative L2 distance of the benchmark spec's tolerance, every field and
+Besides a relative L2 distance of at most 1e-4, every field and
 trace set must also agree point by point to 1e-4 of its largest magnitude,
 so that one wrong point cannot hide in a large array.
 """
@@ -81,7 +81,7 @@ def test_tti_full_window(so):
     Ricker source, receivers on every surface node) at 96^3 with an 8-point
     border, the full 1000 ms: 418 steps.
 
-    The traces are held to the benchmark spec's 1e-4.  The final fields are held to
+    The traces are held to a relative L2 distance of 1e-4.  The final fields are held to
     the oracle's FP32 storage model: where eps = delta (a third of the points
     in this recipe) the pseudo-acoustic system has a non-propagating mode,
     w = p - s r with w_tt = 0, which integrates every rounding of the stored
