@@ -792,37 +792,53 @@ def run_serving_only(args):
 
 
 def run_batched_probe(args):
-    """Diagnostic (not the benchmark line): one acoustic forward of S shots
-    sharing a two-layer 256^3 model (so 8, nt 4, one source and one receiver
-    per shot), then three 12-step calls timed with the library's per-launch
-    events; prints the stencil kernel's rate over all shots.  Used to capture
-    the DRAM bytes per shot-point of a shot-batched launch with ncu."""
+    """Diagnostic (not the benchmark line): one forward of S shots sharing a
+    two-layer n^3 model (acoustic, or TTI with the benchmark's anisotropy
+    recipe; space order --batched-so, nt 4, one source and one receiver per
+    shot), then three 12-step calls timed with the library's per-launch
+    events; prints the stencil kernels' time per step and rate over all
+    shots.  Used to capture the DRAM bytes per shot-point of a shot-batched
+    launch with ncu."""
     import torch
     import paper_1807_03032_gb300 as fd
     from paper_1807_03032_gb300 import _native
-    S, n, h = args.batched_probe, args.batched_n, 20.0
+    S, n, h, so = args.batched_probe, args.batched_n, 20.0, args.batched_so
+    tti = args.batched_kind == "tti"
     shape = (n, n, n)
     m = workloads.slowness_squared(workloads.two_layer_velocity(shape, 1.5, 2.5))
     damp = workloads.damping_profile(shape, 20, (h, h, h), 2.5)
-    dt = workloads.cfl_dt((h, h, h), 2.5)
-    c = (n / 2 - 0.5) * h
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    if tti:
+        aniso = [T(f) for f in workloads.tti_fields(shape)]
+        dt = workloads.cfl_dt((h, h, h), 2.5, eps_max=float(aniso[0].max()))
+        fams = ("tti_pass1", "tti_pass2", "tti_fused")
+    else:
+        dt = workloads.cfl_dt((h, h, h), 2.5)
+        fams = ("acoustic_step",)
+    c = (n / 2 - 0.5) * h
     g = fd.Grid(shape, (h, h, h))
     mt, dd = T(m), T(damp)
     sx = T(np.tile(np.array([c, c, 30 * h]), (S, 1, 1)))
     rx = T(np.tile(np.array([[c, c, 25 * h]]), (S, 1, 1)))
-    for nt in (4, 12, 12, 12):
-        if nt == 12 and not _native.stats_get("acoustic_step")[1]:
+    for i, nt in enumerate((4, 12, 12, 12)):
+        if i == 1:
+            torch.cuda.synchronize()
             _native.stats_reset()
             _native.stats_enable(True)
         sw = T(np.tile(workloads.ricker(nt, dt)[None, :, None], (S, 1, 1)))
-        fd.acoustic_forward(g, 8, dt, nt, mt, sx, sw, rx, damp=dd, return_final=False)
+        if tti:
+            fd.tti_forward(g, so, dt, nt, mt, *aniso, sx, sw, rx, damp=dd, return_final=False)
+        else:
+            fd.acoustic_forward(g, so, dt, nt, mt, sx, sw, rx, damp=dd, return_final=False)
     torch.cuda.synchronize()
-    ms, k, pts = _native.stats_get("acoustic_step")
+    st = [_native.stats_get(f) for f in fams]
     _native.stats_enable(False)
-    print(json.dumps({"probe": "batched shots", "shots": S, "grid": n, "so": 8,
-                      "kernel_us": round(ms / k * 1e3, 1),
-                      "kernel_gpts_all_shots": round(pts / (ms / k * 1e-3) / 1e9, 1)}), flush=True)
+    steps = max(k for _, k, _ in st)
+    ms = sum(t for t, _, _ in st) / steps
+    pts = max(p for _, _, p in st)
+    print(json.dumps({"probe": "batched shots", "kind": args.batched_kind, "shots": S,
+                      "grid": n, "so": so, "kernel_us_per_step": round(ms * 1e3, 1),
+                      "kernel_gpts_all_shots": round(pts / (ms * 1e-3) / 1e9, 1)}), flush=True)
 
 
 def cpu_baseline(w, so_list):
@@ -936,8 +952,10 @@ def main():
     ap.add_argument("--fwi-n", type=int, default=256)
     ap.add_argument("--fwi-nt", type=int, default=2000)
     ap.add_argument("--batched-probe", type=int, default=0, metavar="S",
-                    help="diagnostic only: one forward of S shots on a 256^3 so-8 model")
+                    help="diagnostic only: one forward of S shots on a 256^3 model")
     ap.add_argument("--batched-n", type=int, default=256)
+    ap.add_argument("--batched-so", type=int, default=8)
+    ap.add_argument("--batched-kind", choices=("acoustic", "tti"), default="acoustic")
     ap.add_argument("--serving-only", action="store_true",
                     help="run only the served shot stream (with --serve-jobs jobs)")
     args = ap.parse_args()
