@@ -78,10 +78,10 @@ __device__ __noinline__ void inject_column(const AcousticStepArgs *a, const Acou
                                            int zchunk, int nzc) {
     const int n = inj->step + (inj->step_base ? *inj->step_base : 0);
     if (n < 0 || n >= inj->nt) return;
-    const int shot = blockIdx.y / nzc;
-    const int za = (blockIdx.y - shot * nzc) * zchunk;
+    const int shot = blockIdx.z / nzc;
+    const int za = (blockIdx.z - shot * nzc) * zchunk;
     const int zb = min(a->L.nz, za + zchunk);
-    const int x0 = blockIdx.x * BX, y0 = blockIdx.z * BY;
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
     const int x1 = min(x0 + BX, a->L.nx), y1 = min(y0 + BY, a->L.ny);
     float *u = a->wave + (int64_t)(shot * a->lps + a->lev_out) * a->L.vol;
     for (int s = 0; s < inj->nsrc; ++s) {
@@ -133,14 +133,10 @@ __global__ void __launch_bounds__(TX *TY, MINB)
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int tx = tid % TX, ty = tid / TX;
-    // launch order: x tiles, then (shot, z chunk), then y tiles, so that the
-    // CTAs of one column of all shots start close together and b's tiles,
-    // read by each of them, come from L2 after the first, while the x
-    // neighbours of a column stay adjacent
-    const int shot_i = blockIdx.y / nzc;
-    const int chunk = blockIdx.y - shot_i * nzc;
+    const int shot_i = blockIdx.z / nzc;
+    const int chunk = blockIdx.z - shot_i * nzc;
     const int shot = a.slot_map ? a.slot_map[shot_i] : shot_i;
-    const int x0 = blockIdx.x * C::BX, y0 = blockIdx.z * C::BY;
+    const int x0 = blockIdx.x * C::BX, y0 = blockIdx.y * C::BY;
     const int za = chunk * zchunk;
     const int zb = min(a.L.nz, za + zchunk);
     const int nplanes = zb - za + 2 * R;  // arriving planes za-R .. zb+R-1
@@ -517,8 +513,13 @@ fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots,
     const int64_t slots = (int64_t)nsm * per_sm;
     // Split z only when the columns alone cannot fill the machine; keep every
     // chunk long enough that the 2R-plane warm-up stays a small fraction.
+    // The narrow stencils (R <= 2) run at the HBM limit once three quarters
+    // of the slots are busy, so there a split only adds warm-up planes
+    // (512^3, so 4: 413 GPts/s unsplit, 396 in two chunks); the wider ones
+    // are limited per SM and gain from the finer units (so 8: 381 in two
+    // chunks, 357 unsplit).
     int nzc = 1;
-    if (cols < slots) {
+    if (cols < slots && !(radius <= 2 && 4 * cols >= 3 * slots)) {
         nzc = (int)((slots + cols - 1) / cols);
         const int min_chunk = 8 * radius > 32 ? 8 * radius : 32;
         const int max_nzc = L.nz / min_chunk > 1 ? L.nz / min_chunk : 1;
@@ -528,7 +529,7 @@ fd_status acoustic_plan(int radius, int config, const WaveLayout &L, int nshots,
     nzc = (L.nz + zchunk - 1) / zchunk;
     if ((int64_t)nshots * nzc > 65535 || nty > 65535)
         return set_error(FD_ERR_ARG, "grid too large for the launch configuration");
-    plan->grid = dim3(ntx, nshots * nzc, nty);
+    plan->grid = dim3(ntx, nty, nshots * nzc);
     plan->zchunk = zchunk;
     plan->nzc = nzc;
     plan->smem = e.smem + (size_t)zchunk * 4;

@@ -293,6 +293,9 @@ struct TtiPlan {
     int zchunk = 0, nzc = 1;
 };
 
+// z chunks per column of the TTI kernels (machine filling and SM balance)
+int tti_z_chunks(int64_t cols, int64_t slots, int nz, int min_chunk);
+
 // coef: 6 consecutive fields b, a, s, n_x, n_y, n_z ([6][vol]).  scheme
 // kTtiTwoPass: K2a writes the six first-derivative temporaries and K2b
 // differentiates them again; kTtiRecompute: one kernel recomputes the inner

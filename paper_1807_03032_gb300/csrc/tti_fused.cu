@@ -393,13 +393,7 @@ fd_status tti_fused_plan(int radius, int stag, const WaveLayout &L, int nshots, 
     const int bx = 64, by = in.by;
     const int ntx = (L.nx + bx - 1) / bx, nty = (L.ny + by - 1) / by;
     const int64_t cols = (int64_t)ntx * nty * nshots, slots = (int64_t)nsm * per_sm;
-    int nzc = 1;
-    if (cols < slots) {
-        nzc = (int)((slots + cols - 1) / cols);
-        const int min_chunk = 16 * radius > 32 ? 16 * radius : 32;
-        const int max_nzc = L.nz / min_chunk > 1 ? L.nz / min_chunk : 1;
-        if (nzc > max_nzc) nzc = max_nzc;
-    }
+    int nzc = tti_z_chunks(cols, slots, L.nz, 16 * radius > 32 ? 16 * radius : 32);
     const int zchunk = (L.nz + nzc - 1) / nzc;
     nzc = (L.nz + zchunk - 1) / zchunk;
     if ((int64_t)nshots * nzc > 65535 || nty > 65535)
