@@ -442,22 +442,22 @@ __global__ void __launch_bounds__(kRecBX *kRecBY) tti_recompute_kernel(const Tti
 
 // ---------------------------------------------------------------- host side
 
-constexpr int kTX = 16, kTY = 8;  // 64 x 8 tile, two groups of 128 threads
+constexpr int kTX = 16, kTY = 8;  // 64 x 8 tile, two groups of 128 threads (64 x 4 at R = 8)
 
 // Launch configurations of the two passes: prefetch depths D1, D2 and the
 // unroll U of the plane loop (the pending z-outputs rotate by one register
 // per plane; unrolling turns the moves into renaming).  Pass 2 stages carry
 // eleven tiles, so a shallower ring keeps more CTAs per SM.
-template <int R, int STAG, int D1_, int D2_, int U_>
+template <int R, int STAG, int D1_, int D2_, int U_, int TYV = kTY>
 struct TtiKernels {
     static constexpr int D1 = D1_;
     static constexpr int D2 = D2_;
     static constexpr int K1 = STAG ? 1 : 0;   // inner derivative: D+ or centred
     static constexpr int K2 = STAG ? -1 : 0;  // outer derivative: D- or centred
-    using C1 = TtiCfg<R, kTX, kTY, D1>;
-    using C2 = TtiCfg<R, kTX, kTY, D2>;
-    static const void *p1() { return (const void *)&tti_pass1_kernel<R, kTX, kTY, D1, K1, U_>; }
-    static const void *p2() { return (const void *)&tti_pass2_kernel<R, kTX, kTY, D2, K2, U_>; }
+    using C1 = TtiCfg<R, kTX, TYV, D1>;
+    using C2 = TtiCfg<R, kTX, TYV, D2>;
+    static const void *p1() { return (const void *)&tti_pass1_kernel<R, kTX, TYV, D1, K1, U_>; }
+    static const void *p2() { return (const void *)&tti_pass2_kernel<R, kTX, TYV, D2, K2, U_>; }
     static const void *rc() { return (const void *)&tti_recompute_kernel<R, K1, K2>; }
 };
 
@@ -467,9 +467,9 @@ struct TtiInfo {
     int bx, by, pw, ph, threads;
 };
 
-template <int R, int STAG, int D1, int D2, int U>
+template <int R, int STAG, int D1, int D2, int U, int TYV = kTY>
 TtiInfo info_r() {
-    using K = TtiKernels<R, STAG, D1, D2, U>;
+    using K = TtiKernels<R, STAG, D1, D2, U, TYV>;
     using C1 = typename K::C1;
     using C2 = typename K::C2;
     static_assert(C1::BX == C2::BX && C1::BY == C2::BY && C1::THREADS == C2::THREADS, "tiles");
@@ -479,13 +479,16 @@ TtiInfo info_r() {
 
 // Built-in configuration per radius, measured on GB300 at 512^3: a deeper
 // pass-1 prefetch and a 4x unrolled plane loop pay for R = 4 and R = 6
-// (+18 % and +7 %); at R = 8 the unroll costs occupancy (registers).
+// (+18 % and +7 %); at R = 8 the unroll costs occupancy (registers), and
+// 64 x 4 tiles (two groups of 64 threads, twice the columns) run the step
+// 6 % faster than 64 x 8 (2.58 against 2.74 ms; 5-10 % slower at R = 4, 6).
 template <int R>
 struct TtiDefault {
     static constexpr bool MID = R == 4 || R == 6;
     static constexpr int D1 = MID ? 3 : 2;
     static constexpr int D2 = MID ? 2 : (R >= 6 ? 1 : 2);
     static constexpr int U = MID ? 4 : 1;
+    static constexpr int TY = R == 8 ? 4 : kTY;
 };
 
 // Configuration table: index 0 is the built-in choice, the others are kept
@@ -496,21 +499,22 @@ bool tti_info_r(int config, TtiInfo *out) {
     using Df = TtiDefault<R>;
     constexpr int D2d = R >= 6 ? 1 : 2;
     if (STAG) {
-        *out = info_r<R, STAG, Df::D1, Df::D2, Df::U>();
+        *out = info_r<R, STAG, Df::D1, Df::D2, Df::U, Df::TY>();
         return true;
     }
     switch (config) {
-        case 0: *out = info_r<R, 0, Df::D1, Df::D2, Df::U>(); return true;
+        case 0: *out = info_r<R, 0, Df::D1, Df::D2, Df::U, Df::TY>(); return true;
         case 1: *out = info_r<R, 0, 2, D2d, 1>(); return true;
         case 2: *out = info_r<R, 0, 2, D2d, 4>(); return true;
         case 3: *out = info_r<R, 0, 3, 2, 4>(); return true;
         case 4: *out = info_r<R, 0, 1, 1, 4>(); return true;
         case 5: *out = info_r<R, 0, 3, 1, 1>(); return true;
+        case 6: *out = info_r<R, 0, Df::D1, Df::D2, Df::U, Df::TY == 4 ? 8 : 4>(); return true;
         default: return false;
     }
 }
 
-constexpr int kTtiConfigs = 6;
+constexpr int kTtiConfigs = 7;
 
 template <int STAG>
 bool tti_info_s(int radius, int config, TtiInfo *out) {
