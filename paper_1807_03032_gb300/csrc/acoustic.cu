@@ -424,7 +424,7 @@ const ConfigEntry *config_table_df(int radius) {
     static const ConfigEntry r2 = FD_AC_ENTRY_DF(2, 16, 16, 1, 4, 4, 0);
     static const ConfigEntry r4 = FD_AC_ENTRY_DF(4, 16, 8, 1, 3, 4, 0);
     static const ConfigEntry r6 = FD_AC_ENTRY_DF(6, 16, 8, 1, 2, 4, 4);
-    static const ConfigEntry r8 = FD_AC_ENTRY_DF(8, 16, 8, 1, 1, 4, 4);
+    static const ConfigEntry r8 = FD_AC_ENTRY_DF(8, 16, 4, 1, 1, 4, 8);
     switch (radius) {
         case 1: return &r1;
         case 2: return &r2;
