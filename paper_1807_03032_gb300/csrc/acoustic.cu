@@ -415,10 +415,10 @@ const ConfigEntry *config_table_wl(int radius) {
 }
 
 // 3-D damping field: one configuration per radius, the default one's tiles,
-// with the prefetch depth and register bound chosen so that four CTAs fit
-// on an SM despite the fourth interior tile per stage: with fewer, the 512
-// columns of a 512^3 launch need two waves of 456 CTAs (measured: so 8 and
-// 12 at 0.6 of the copy bandwidth with the default depths).
+// with the prefetch depth and register bound chosen so that a 512^3 launch
+// still fits in one wave despite the fourth interior tile per stage (four
+// 128-thread or eight 64-thread CTAs per SM; with three 128-thread CTAs the
+// 512 columns need two waves: so 8 and 12 at 0.6 of the copy bandwidth).
 const ConfigEntry *config_table_df(int radius) {
     static const ConfigEntry r1 = FD_AC_ENTRY_DF(1, 16, 16, 1, 4, 1, 0);
     static const ConfigEntry r2 = FD_AC_ENTRY_DF(2, 16, 16, 1, 4, 4, 0);
