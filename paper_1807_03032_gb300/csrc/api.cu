@@ -985,7 +985,7 @@ static fd_status tti_forward_impl(const fd_grid *grid, int so, double dt, int nt
         return set_error(FD_ERR_ARG, "tti_forward: options (%d, %d, %d) out of range", op.deriv,
                          op.receiver, op.scheme);
     // automatic: the fused kernel where it was measured faster (so <= 4:
-    // 2.02 against 2.41 ms per 512^3 step at so 4), two passes otherwise
+    // 1.76 against 2.12 ms per 512^3 step at so 4), two passes otherwise
     if (op.scheme == FD_TTI_AUTO)
         op.scheme = (so <= 4 && tti_fused_supported(so / 2)) ? FD_TTI_FUSED : FD_TTI_TWO_PASS;
     if (op.scheme == FD_TTI_FUSED && !tti_fused_supported(so / 2))
