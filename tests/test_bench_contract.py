@@ -57,3 +57,26 @@ def test_recorded_traffic_is_reported_only_for_the_kernel_it_was_measured_on(mon
                    - 1.0) < 0.05
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
     assert bench.ncu_traffic() is None
+
+
+def test_kernel_hash_ignores_comment_lines_but_not_code(tmp_path, monkeypatch):
+    """A whole-line comment edit keeps the hash (the kernel is unchanged); an
+    edit of a code line, or of a comment at the end of a code line, changes
+    it."""
+    import shutil
+    src = os.path.join(ROOT, "paper_1807_03032_gb300", "csrc")
+    dst = tmp_path / "paper_1807_03032_gb300" / "csrc"
+    dst.mkdir(parents=True)
+    for f in ("acoustic.cu", "acoustic2.cu", "f32x2.cuh", "common.cuh", "kernels.cuh"):
+        shutil.copy(os.path.join(src, f), dst / f)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_source_hash()
+    assert h0 == bench.kernel_source_hash()
+    p = dst / "acoustic.cu"
+    text = p.read_text()
+    p.write_text("// a new whole-line comment\n\n" + text.replace("\n//", "\n    // reworded:", 1))
+    assert bench.kernel_source_hash() == h0
+    p.write_text(text.replace("int nzc = 1;", "int nzc = 2;", 1))
+    assert bench.kernel_source_hash() != h0
+    p.write_text(text.replace(";\n", ";  // trailing\n", 1))
+    assert bench.kernel_source_hash() != h0
